@@ -1,0 +1,222 @@
+/*
+ * schur_gb300.h -- C ABI of the GB300 (sm_103a) FP64 Hessenberg -> real Schur
+ * library: multishift QR with aggressive early deflation (AED).
+ *
+ * The method is the one of Myllykoski, "Algorithm 1019: A task-based
+ * multi-shift QR/QZ algorithm with aggressive early deflation", ACM TOMS
+ * 48(1), 2021:
+ *   - Sec. 2.1   the iteration: deflate, decouple, iterate, fail at a limit;
+ *   - Sec. 2.2   shifts and bulge chasing (Fig. 1);
+ *   - Sec. 2.3   tightly-coupled multishift bulge chains chased through
+ *                diagonal windows with an accumulated transform U, applied
+ *                off-window by matrix-matrix products (Fig. 2, Fig. 3);
+ *   - Sec. 2.5   aggressive early deflation (Fig. 4);
+ *   - Sec. 5.6   the deflation conditions (LAPACK-style, norm-stable, fixed).
+ * The real Schur form is eq. (schur_form) with the 2x2 blocks of
+ * eq. (2by2_blocks), returned in standardised form (equal diagonal entries,
+ * off-diagonal entries of opposite sign).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are FP64, column-major, with a leading dimension ld >= n
+ *    (entry (i, j) at p[i + j * ld]).
+ *  - Every matrix / vector pointer is a DEVICE pointer owned by the caller,
+ *    unless the argument's comment says "host".  The library never frees
+ *    caller memory.
+ *  - Work is issued on opts->stream (a cudaStream_t; NULL = the legacy default
+ *    stream).  The functions return after the result is complete (they read
+ *    a few control scalars back from the device during the iteration).
+ *  - Scratch: if opts->workspace is non-NULL and opts->workspace_bytes is at
+ *    least the size reported by the matching *_workspace_size call, the
+ *    library allocates no device memory; otherwise it allocates (and frees)
+ *    its own scratch inside the call.
+ *  - Return codes: SCHUR_OK (0) on success; a negative value -(i) when
+ *    argument i (1-based) is invalid; SCHUR_ERR_* below for other errors;
+ *    a positive value k > 0 when the iteration limit was reached: rows
+ *    0..k-1 may still contain unreduced blocks (H and Z then hold a valid
+ *    orthogonal similarity of the input, as in LAPACK's dhseqr).
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef SCHUR_GB300_H
+#define SCHUR_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCHUR_OK 0
+#define SCHUR_ERR_NONFINITE (-1001) /* H contains NaN or Inf */
+#define SCHUR_ERR_CUDA (-1002)      /* a CUDA runtime call failed */
+#define SCHUR_ERR_NOMEM (-1003)     /* scratch allocation failed */
+#define SCHUR_ERR_WORKSPACE (-1004) /* caller workspace too small */
+#define SCHUR_ERR_UNSUPPORTED (-1005)
+
+/* Deflation conditions of Sec. 5.6. */
+#define SCHUR_DEFLATION_LAPACK 0 /* item 1 (the paper's experiments) */
+#define SCHUR_DEFLATION_NORM 1   /* item 2, norm-stable */
+#define SCHUR_DEFLATION_FIXED 2  /* item 3, |entry| <= fixed_thold */
+
+typedef struct {
+  int struct_size;     /* sizeof(schur_opts); set by schur_default_opts */
+  int n_shifts;        /* shifts per sweep (even); 0 = size table */
+  int aed_window;      /* AED window nw; 0 = size table */
+  int bulges_per_chain;/* bulges chased together in one window; 0 = auto */
+  int nmin;            /* blocks of at most nmin rows use double-shift QR; 0 = 75 */
+  int nibble;          /* repeat AED when it deflates > nibble % of nw; 0 = 14 */
+  int deflation;       /* SCHUR_DEFLATION_* */
+  double fixed_thold;  /* threshold for SCHUR_DEFLATION_FIXED */
+  int want_z;          /* 1: accumulate Z (default), 0: Z is not referenced */
+  int z_init;          /* 0: Z is set to I on entry; 1: Z holds Q1 and is
+                          multiplied in place (Z <- Z * Z_QR) */
+  void* stream;        /* cudaStream_t */
+  void* workspace;     /* optional device scratch (see conventions) */
+  size_t workspace_bytes;
+} schur_opts;
+
+/* Statistics of the last schur_hessenberg call on this host thread. */
+typedef struct {
+  int aed_steps;        /* AED steps (Sec. 2.5) at the top level */
+  int sweeps;           /* multishift sweeps (Sec. 2.3) at the top level */
+  int small_qr;         /* blocks finished by double-shift QR (Sec. 2.2) */
+  int deflated_by_aed;  /* eigenvalues deflated by AED at the top level */
+  int window_launches;  /* bulge-chase window launches (all levels) */
+  double sweep_gemm_flops;  /* executed FP64 flops of the off-window updates */
+  double aed_gemm_flops;
+  double reflector_flops;   /* algorithmic flops of direct reflector application */
+} schur_stats;
+
+/* Fill *opts with the defaults listed above. Returns SCHUR_OK. */
+int schur_default_opts(schur_opts* opts);
+
+/* Human-readable text for a return code (static storage). */
+const char* schur_status_string(int code);
+
+/* Device scratch (bytes) needed by schur_hessenberg for order n and *opts
+ * (opts may be NULL for the defaults). */
+int schur_workspace_size(int n, const schur_opts* opts, size_t* bytes);
+
+/*
+ * schur_hessenberg -- reduce the upper Hessenberg H (n x n) to real Schur form
+ * S = Z^T H Z (Sec. 2, eqs. hessenberg_form .. 2by2_blocks).
+ *   n      order, n >= 0                                            (arg 1)
+ *   H      device, ldh x n; on entry the upper Hessenberg matrix (entries
+ *          below the first subdiagonal are ignored); on exit S, standardised
+ *          quasi-triangular, zero below the subdiagonal                (arg 2)
+ *   ldh    >= max(1, n)                                             (arg 3)
+ *   Z      device, ldz x n; see opts->z_init; on exit Z_in * Z_QR; may be
+ *          NULL when opts->want_z == 0                              (arg 4)
+ *   ldz    >= max(1, n) when Z is referenced                        (arg 5)
+ *   wr,wi  device, length n: eigenvalues; a complex pair is adjacent with
+ *          the positive imaginary part first (the order of S's diagonal)
+ *                                                                    (args 6, 7)
+ *   opts   may be NULL (defaults)                                   (arg 8)
+ */
+int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, double* wr, double* wi,
+                     const schur_opts* opts);
+
+/* Statistics of the last schur_hessenberg call made by this host thread. */
+int schur_last_stats(schur_stats* out);
+
+/*
+ * schur_hessenberg_batched -- the same reduction for `batch` independent
+ * matrices of uneven sizes in ONE persistent kernel launch, replayed from a
+ * captured CUDA graph (not in the paper: batching of the method).  Each
+ * matrix is reduced by one thread block with the same iteration as
+ * schur_hessenberg (AED, multishift sweeps, double-shift QR for small
+ * blocks, the same deflation conditions), with reflectors applied directly
+ * instead of through windows.
+ *   batch        number of matrices, >= 0                            (arg 1)
+ *   n            host array [batch]: orders, 1 <= n[b] <= 1024          (arg 2)
+ *   H            host array [batch] of device pointers (as in schur_hessenberg)
+ *   ldh          host array [batch]
+ *   Z            host array [batch] of device pointers (always accumulated;
+ *                opts->z_init applies)                               (arg 5)
+ *   ldz          host array [batch]
+ *   wr, wi       host arrays [batch] of device pointers, length n[b] each
+ *   info         host array [batch] (output): per-matrix status as in
+ *                schur_hessenberg                                     (arg 9)
+ *   opts         may be NULL                                          (arg 10)
+ * Returns SCHUR_OK if the launch succeeded (check info[] per matrix).
+ */
+int schur_hessenberg_batched(int batch, const int* n, double* const* H, const int* ldh, double* const* Z,
+                             const int* ldz, double* const* wr, double* const* wi, int* info,
+                             const schur_opts* opts);
+
+/*
+ * schur_eig_backward -- adjoint of the eigenvalues (not in the paper).  For
+ * a real loss L(lambda_1..lambda_n) with cotangents g_k = dL/dRe(lambda_k) +
+ * i dL/dIm(lambda_k), returns dL/dH = Z G Z^T with
+ *     G = Re( sum_k conj(g_k) / (y_k^H x_k) * conj(y_k) x_k^T ),
+ * x_k, y_k the right / left eigenvectors of S (first-order eigenvalue
+ * perturbation: d lambda = y^H dH x / y^H x).  The eigenvectors come from
+ * block back / forward substitution on the quasi-triangular S.
+ *   n          order                                                (arg 1)
+ *   S, lds     device, the standardised Schur factor from schur_hessenberg
+ *   Z, ldz     device, the Schur vectors from schur_hessenberg       (args 4, 5)
+ *   wr, wi     device, eigenvalues in S's order                      (args 6, 7)
+ *   gwr, gwi   device, length n: cotangents of Re / Im of each eigenvalue
+ *   dH, lddh   device, output n x n                                  (args 10, 11)
+ *   opts       may be NULL (stream, workspace)                        (arg 12)
+ */
+int schur_eig_backward(int n, const double* S, int lds, const double* Z, int ldz, const double* wr,
+                       const double* wi, const double* gwr, const double* gwi, double* dH, int lddh,
+                       const schur_opts* opts);
+
+/* schur_eig_backward for `batch` matrices in one launch sequence; arrays as
+ * in schur_hessenberg_batched (host arrays of device pointers). */
+int schur_eig_backward_batched(int batch, const int* n, double* const* S, const int* lds, double* const* Z,
+                               const int* ldz, double* const* wr, double* const* wi, double* const* gwr,
+                               double* const* gwi, double* const* dH, const int* lddh,
+                               const schur_opts* opts);
+
+/* ---------------------------------------------------------------------
+ * Single steps of the method, exported so that each can be checked on its
+ * own against the CPU oracle.  Same conventions as above.
+ * --------------------------------------------------------------------- */
+
+/*
+ * schur_sweep -- one tightly-coupled multishift sweep (Sec. 2.3, Fig. 2/3)
+ * on the unreduced block rows/cols ilo..ihi (0-based, inclusive) of the
+ * n x n H, full Schur form mode (rows 0.. and columns ..n-1 are updated,
+ * and Z's columns ilo..ihi when Z != NULL).
+ *   pairs  HOST array of 2*npairs doubles: (s1+s2, s1*s2) for each shift
+ *          pair; pair b drives the b-th bulge introduced.          (arg 8)
+ *   bulges_per_chain: bulges chased together in one window (0 = auto).
+ */
+int schur_sweep(int n, double* H, int ldh, double* Z, int ldz, int ilo, int ihi, const double* pairs,
+                int npairs, int bulges_per_chain, const schur_opts* opts);
+
+/*
+ * schur_aed -- one AED step (Sec. 2.5) on the trailing nw x nw window of the
+ * active block ktop..kbot (0-based, inclusive).  On exit *nd (host) is the
+ * number of deflated eigenvalues; cand_re / cand_im (HOST arrays of length
+ * >= nw) receive the undeflated candidates top to bottom and *ncand (host)
+ * their count.  H and Z are updated in place (window written back only if
+ * *nd > 0).
+ */
+int schur_aed(int n, double* H, int ldh, double* Z, int ldz, int ktop, int kbot, int nw, int* nd,
+              double* cand_re, double* cand_im, int* ncand, const schur_opts* opts);
+
+/*
+ * schur_small_qr -- double-shift QR (Sec. 2.2) of the block ilo..ihi, full
+ * Schur form mode, run by one thread block (the "small Schur" step used for
+ * blocks of at most nmin rows; ihi - ilo + 1 <= 160).
+ */
+int schur_small_qr(int n, double* H, int ldh, double* Z, int ldz, int ilo, int ihi, const schur_opts* opts);
+
+/*
+ * schur_apply_u -- off-window update (Sec. 3.2.1 "left/right update"):
+ * side 0: X <- U^T X with X = rows r0..r0+k-1, columns c0..c0+m-1 of A;
+ * side 1: X <- X U   with X = rows r0..r0+m-1, columns c0..c0+k-1 of A.
+ * U is k x k (device, ldu).  1 <= k <= 1024.
+ */
+int schur_apply_u(int side, double* A, int lda, int r0, int c0, int m, int k, const double* U, int ldu,
+                  const schur_opts* opts);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCHUR_GB300_H */

@@ -54,6 +54,7 @@ class Params:
     deflation: str = "lapack"
     thold: float = 0.0
     exc_period: int = 6
+    nwin_francis: int = 160  # AED windows up to this order: Francis QR
     normH: float = 0.0  # ||H||_F of the input, set by ``schur``
     depth: int = 0      # AED recursion depth (0 = the input matrix)
 
@@ -61,8 +62,8 @@ class Params:
         """Parameters for the recursive QR inside an AED window: same
         deflation mode, default shift/window table, one level deeper."""
         return Params(ns=0, nw=0, nmin=self.nmin, nibble=self.nibble, deflation=self.deflation,
-                      thold=self.thold, exc_period=self.exc_period, normH=self.normH,
-                      depth=self.depth + 1)
+                      thold=self.thold, exc_period=self.exc_period, nwin_francis=self.nwin_francis,
+                      normH=self.normH, depth=self.depth + 1)
 
 
 def default_ns_nw(m):
@@ -82,7 +83,7 @@ def default_ns_nw(m):
     if m < 6000:
         return 64, 128
     ns = 256
-    return ns, max(3 * ns // 2, int(round(0.03 * m)))
+    return ns, min(1024, max(3 * ns // 2, int(round(0.03 * m))))
 
 
 # --------------------------------------------------------------------------
@@ -484,9 +485,11 @@ def aed(H, Z, ktop, kbot, nw, P, n=None):
     [ktop, kbot] (Sec. 2.5):
 
     1. the window T is copied out and reduced to Schur form T = V T_S V^T by
-       recursive QR (this driver; Francis double-shift QR when nw <= nmin or
-       when T is itself the window of a window -- reading: the paper says
-       "recursive application of the QR algorithm" without a depth);
+       recursive QR (this driver; Francis double-shift QR when nw is at most
+       max(nmin, nwin_francis) or when T is itself the window of a window --
+       reading: the paper says "recursive application of the QR algorithm"
+       without a size or depth rule; nwin_francis = 160 is the largest window
+       one GPU thread block holds in shared memory);
     2. with s = h_{kwtop, kwtop-1} the spike is s * V[0, :]; candidates are
        tested bottom-up (``spike_deflatable``); a failed block is moved to
        the top of the unevaluated part (``move_block_up``); a rejected swap
@@ -508,7 +511,7 @@ def aed(H, Z, ktop, kbot, nw, P, n=None):
     T = np.triu(H[kwtop:kbot + 1, kwtop:kbot + 1], -1).copy()
     V = np.eye(nw)
     Pw = P.for_window()
-    if nw <= P.nmin or Pw.depth >= MAX_DEPTH:
+    if nw <= max(P.nmin, P.nwin_francis) or Pw.depth >= MAX_DEPTH:
         info = francis_qr(T, V, 0, nw - 1, Pw, nw)
     else:
         info = qr_block(T, V, 0, nw - 1, Pw, nw)

@@ -1,0 +1,687 @@
+// driver.cu -- host driver and C ABI of the single-matrix path.
+//
+// The iteration of Sec. 2.1 runs on the host as a short control loop over
+// device-resident data; every arithmetic step is a kernel of kernels.cu.  Per
+// iteration the host reads back one small control block (Ctl) twice: after
+// the deflation scan (where the bottom unreduced block starts) and after AED
+// (how many eigenvalues deflated, how many shift pairs are ready).  A sweep is
+// then issued without further synchronisation as a sequence of window steps:
+// one k_chase launch (one block per bulge chain, Sec. 2.4) followed by the
+// off-window products, H-left plus Z first, then H-right (the two overlap on
+// blocks H[window_i, window_j], where left and right products commute).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/schur_gb300.h"
+#include "kernels.cuh"
+#include "host.h"
+
+namespace schur {
+
+thread_local schur_stats g_stats;
+
+const char* status_string(int code) {
+  switch (code) {
+    case SCHUR_OK: return "success";
+    case SCHUR_ERR_NONFINITE: return "input contains NaN or Inf";
+    case SCHUR_ERR_CUDA: return "CUDA runtime error";
+    case SCHUR_ERR_NOMEM: return "device memory allocation failed";
+    case SCHUR_ERR_WORKSPACE: return "workspace too small";
+    case SCHUR_ERR_UNSUPPORTED: return "unsupported argument combination";
+    default: break;
+  }
+  if (code < 0) return "invalid argument";
+  return "iteration limit reached (unreduced blocks remain)";
+}
+
+// Default (shifts, AED window) for an active block of m rows.  The paper has
+// no table (windows are sized by tiles, Sec. 3.2); the same table is used by
+// the oracle.
+void default_ns_nw(int m, int* ns, int* nw) {
+  if (m < 150) { *ns = 8; *nw = 24; return; }
+  if (m < 590) { *ns = 8; *nw = 32; return; }
+  if (m < 3000) { *ns = 64; *nw = 96; return; }
+  if (m < 6000) { *ns = 64; *nw = 128; return; }
+  *ns = 256;
+  *nw = std::min(1024, std::max(3 * 256 / 2, (int)std::lround(0.03 * m)));
+}
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct LevelSizes {
+  int n;       // order of the matrix at this level
+  int nwmax;   // largest AED window
+  int nsmax;   // most shifts
+  size_t bytes() const {
+    size_t b = 0;
+    b += align_up(sizeof(Ctl));
+    b += align_up((size_t)MAX_CHAINS * KWIN_MAX * KWIN_MAX * sizeof(double));  // chase U
+    b += align_up((size_t)nwmax * nwmax * sizeof(double));                       // V
+    b += (nwmax > NW_SMEM_MAX) ? align_up((size_t)nwmax * nwmax * sizeof(double)) : 0;  // T
+    b += 2 * align_up((size_t)std::max(nwmax, 4) * sizeof(double));              // candidates
+    b += align_up((size_t)(nsmax + 8) * sizeof(double));                         // pairs
+    b += align_up((size_t)4 * std::max(nwmax, 4) * sizeof(double));              // vbuf
+    b += align_up((size_t)NW_SMEM_MAX * NW_SMEM_MAX * sizeof(double));           // small-QR U
+    return b;
+  }
+};
+
+static void level_plan(int n, const schur_opts& o, std::vector<LevelSizes>& out) {
+  out.clear();
+  int m = n;
+  for (int lev = 0; lev < 3 && m > 0; ++lev) {
+    int ns, nw;
+    default_ns_nw(m, &ns, &nw);
+    if (lev == 0) {
+      if (o.n_shifts > 0) ns = o.n_shifts;
+      if (o.aed_window > 0) nw = o.aed_window;
+    }
+    nw = std::min(std::min(nw, m), 1024);
+    LevelSizes L{m, nw, ns};
+    out.push_back(L);
+    if (nw <= NW_SMEM_MAX) break;
+    m = nw;
+  }
+}
+
+size_t workspace_bytes(int n, const schur_opts& o) {
+  std::vector<LevelSizes> lv;
+  level_plan(n, o, lv);
+  size_t b = align_up(sizeof(int)) + 256;
+  for (auto& L : lv) b += L.bytes();
+  return b;
+}
+
+void Solver::carve(char* base, int n) {
+  std::vector<LevelSizes> lv;
+  level_plan(n, opts, lv);
+  char* p = base;
+  auto take = [&](size_t bytes) {
+    char* q = p;
+    p += align_up(bytes);
+    return q;
+  };
+  flag = (int*)take(sizeof(int));
+  levels.clear();
+  for (auto& L : lv) {
+    Level v;
+    v.n = L.n;
+    v.nwmax = L.nwmax;
+    v.nsmax = L.nsmax;
+    v.ctl = (Ctl*)take(sizeof(Ctl));
+    v.ubuf = (double*)take((size_t)MAX_CHAINS * KWIN_MAX * KWIN_MAX * sizeof(double));
+    v.V = (double*)take((size_t)L.nwmax * L.nwmax * sizeof(double));
+    v.T = (L.nwmax > NW_SMEM_MAX) ? (double*)take((size_t)L.nwmax * L.nwmax * sizeof(double)) : nullptr;
+    v.cand_re = (double*)take((size_t)std::max(L.nwmax, 4) * sizeof(double));
+    v.cand_im = (double*)take((size_t)std::max(L.nwmax, 4) * sizeof(double));
+    v.pairs = (double*)take((size_t)(L.nsmax + 8) * sizeof(double));
+    v.vbuf = (double*)take((size_t)4 * std::max(L.nwmax, 4) * sizeof(double));
+    v.usmall = (double*)take((size_t)NW_SMEM_MAX * NW_SMEM_MAX * sizeof(double));
+    levels.push_back(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Solver
+// ---------------------------------------------------------------------------
+static bool g_attr_done = false;
+static int g_num_sms = 0;
+
+static void ck(cudaError_t e) {
+  if (e != cudaSuccess) throw CudaError{e};
+}
+
+void init_kernel_attributes() {
+  if (g_attr_done) return;
+  int dev = 0;
+  ck(cudaGetDevice(&dev));
+  ck(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+  const int big = 220 * 1024;
+  ck(cudaFuncSetAttribute(k_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  ck(cudaFuncSetAttribute(k_smallqr, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  ck(cudaFuncSetAttribute(k_aed_small, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  ck(apply_u_set_smem(big));
+  g_attr_done = true;
+}
+
+int num_sms() { return g_num_sms > 0 ? g_num_sms : 152; }
+
+Solver::Solver(const schur_opts* o) {
+  schur_default_opts(&opts);
+  if (o) {
+    size_t sz = std::min((size_t)o->struct_size, sizeof(schur_opts));
+    if (sz == 0) sz = sizeof(schur_opts);
+    memcpy(&opts, o, sz);
+  }
+  st = (cudaStream_t)opts.stream;
+  if (opts.nmin <= 0) opts.nmin = 75;
+  if (opts.nmin > NW_SMEM_MAX) opts.nmin = NW_SMEM_MAX;
+  if (opts.nibble <= 0) opts.nibble = 14;
+  ck(cudaMallocHost((void**)&hctl, sizeof(Ctl)));
+}
+
+Solver::~Solver() {
+  if (hctl) cudaFreeHost(hctl);
+  if (owned) cudaFree(owned);
+}
+
+int Solver::setup(int n) {
+  init_kernel_attributes();
+  size_t need = workspace_bytes(n, opts);
+  char* base = nullptr;
+  if (opts.workspace != nullptr) {
+    if (opts.workspace_bytes < need) return SCHUR_ERR_WORKSPACE;
+    base = (char*)opts.workspace;
+  } else {
+    if (cudaMalloc((void**)&owned, need) != cudaSuccess) {
+      owned = nullptr;
+      cudaGetLastError();
+      return SCHUR_ERR_NOMEM;
+    }
+    base = (char*)owned;
+  }
+  carve(base, n);
+  return SCHUR_OK;
+}
+
+void Solver::read_ctl(const Ctl* dctl) {
+  ck(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  ck(cudaStreamSynchronize(st));
+}
+
+DeflParams Solver::defl(int n) const {
+  DeflParams d;
+  d.mode = opts.deflation;
+  d.thold = opts.fixed_thold;
+  d.normH = normH;
+  d.n = n;
+  return d;
+}
+
+// Issue a list of off-window products (split in launches of at most
+// MAX_UPD_TASKS tasks; tasks within a launch must not overlap).
+void Solver::run_updates(std::vector<UpdTask>& tasks) {
+  size_t i = 0;
+  while (i < tasks.size()) {
+    UpdArgs a;
+    memset(&a, 0, sizeof(a));
+    int maxL = 1;
+    int cnt = 0;
+    for (; i < tasks.size() && cnt < MAX_UPD_TASKS; ++i) {
+      if (tasks[i].nvec <= 0 || tasks[i].L <= 0) continue;
+      a.t[cnt++] = tasks[i];
+      maxL = std::max(maxL, tasks[i].L);
+    }
+    if (cnt == 0) continue;
+    a.ntask = cnt;
+    int tn = apply_u_tn(maxL);
+    a.tn = tn;
+    int tile = 0;
+    for (int t = 0; t < cnt; ++t) {
+      a.t[t].tile0 = tile;
+      a.t[t].ntile = (a.t[t].nvec + tn - 1) / tn;
+      tile += a.t[t].ntile;
+      double f = 2.0 * a.t[t].L * (double)a.t[t].L * a.t[t].nvec;
+      if (cur_flops) *cur_flops += f;
+    }
+    size_t smem = apply_u_smem_bytes(tn, maxL);
+    int per_sm = std::max(1, (int)((226 * 1024) / std::max<size_t>(smem, 1)));
+    int grid = std::min(tile, num_sms() * std::min(per_sm, 8));
+    ck(launch_apply_u(tn, grid, smem, st, a));
+  }
+}
+
+static UpdTask make_task(double* A, long long lda, int side, int r0, int c0, int L, int nvec, const double* U, int ldu,
+                         const int* gate) {
+  UpdTask t;
+  memset(&t, 0, sizeof(t));
+  t.A = A;
+  t.lda = lda;
+  t.side = side;
+  t.r0 = r0;
+  t.c0 = c0;
+  t.L = L;
+  t.nvec = nvec;
+  t.U = U;
+  t.ldu = ldu;
+  t.gate = gate;
+  return t;
+}
+
+// Apply an accumulated L x L transform of the diagonal block [k0, k0+L) to
+// the rest of H (full Schur form: columns right of the block, rows above it)
+// and to Z's columns k0..k0+L-1.
+void Solver::apply_block_transform(const Mat3& M, int k0, int L, const double* U, int ldu, const int* gate) {
+  std::vector<UpdTask> t1, t2;
+  if (k0 + L < M.n) t1.push_back(make_task(M.H, M.ldh, 0, k0, k0 + L, L, M.n - k0 - L, U, ldu, gate));
+  if (M.Z) t1.push_back(make_task(M.Z, M.ldz, 1, 0, k0, L, M.zrows, U, ldu, gate));
+  if (k0 > 0) t2.push_back(make_task(M.H, M.ldh, 1, 0, k0, L, k0, U, ldu, gate));
+  // left products and right products touch H[k0.., k0..] on disjoint sets:
+  // left: rows k0..k0+L-1, columns >= k0+L; right: rows < k0, columns of
+  // the block -- so they can share a launch.
+  for (auto& x : t2) t1.push_back(x);
+  run_updates(t1);
+}
+
+// ---------------------------------------------------------------------------
+// One multishift sweep (Sec. 2.3) on [lo, hi] with npairs pairs (device).
+// ---------------------------------------------------------------------------
+void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs, int npairs, int nbc_req) {
+  Level& Lv = levels[lev];
+  int nbc = nbc_req > 0 ? nbc_req : (opts.bulges_per_chain > 0 ? opts.bulges_per_chain : 16);
+  nbc = std::max(1, std::min(nbc, std::min(npairs, MAX_BULGES_PER_CHAIN)));
+  // every chain in flight must fit one launch (MAX_CHAINS blocks)
+  nbc = std::max(nbc, (npairs + MAX_CHAINS - 1) / MAX_CHAINS);
+  int kwin = std::min(KWIN_MAX, std::max(6 * nbc, 48));
+  int delta = kwin - 3 * nbc - 1;
+  if (delta < 1) {
+    kwin = 3 * nbc + 2;
+    delta = 1;
+  }
+  int nchain = (npairs + nbc - 1) / nbc;
+  int D = kwin + delta + 3 * nbc + 2;
+  int S = (D + delta - 1) / delta;
+  std::vector<int> tend(nchain), nbs(nchain), start(nchain);
+  int last = 0;
+  for (int c = 0; c < nchain; ++c) {
+    nbs[c] = std::min(nbc, npairs - c * nbc);
+    tend[c] = (hi - lo - 1) + 3 * (nbs[c] - 1);
+    start[c] = c * S;
+    int nl = (tend[c] + delta) / delta;  // launches of this chain
+    last = std::max(last, start[c] + nl);
+  }
+  size_t smem = chase_smem_bytes(kwin);
+  for (int s = 0; s < last; ++s) {
+    ChaseArgs a;
+    memset(&a, 0, sizeof(a));
+    a.lo = lo;
+    a.hi = hi;
+    a.ldu = kwin;
+    int na = 0;
+    // chains in order 0 (ahead, lowest) .. nchain-1; process up to
+    // MAX_CHAINS per launch (nchain <= MAX_CHAINS by construction).
+    for (int c = 0; c < nchain && na < MAX_CHAINS; ++c) {
+      if (s < start[c]) continue;
+      int tau0 = (s - start[c]) * delta;
+      if (tau0 > tend[c]) continue;
+      int tau1 = std::min(tau0 + delta, tend[c] + 1);
+      int nb = nbs[c];
+      int kmin = std::max(lo, lo + tau0 - 3 * (nb - 1));
+      int kmax = std::min(hi - 1, lo + tau1 - 1);
+      if (kmin > kmax) continue;
+      ChainDesc& d = a.c[na];
+      d.ws = (kmin == lo) ? lo : kmin - 1;
+      d.we = std::min(kmax + 3, hi);
+      d.tau0 = tau0;
+      d.tau1 = tau1;
+      d.pair0 = c * nbc;
+      d.nb = nb;
+      d.uoff = na * kwin * kwin;
+      ++na;
+    }
+    if (na == 0) continue;
+    a.nchain = na;
+    k_chase<<<na, CTA_THREADS, smem, st>>>(M.H, M.ldh, dpairs, Lv.ubuf, a);
+    ck(cudaGetLastError());
+    g_stats.window_launches += 1;
+    std::vector<UpdTask> t1, t2;
+    for (int i = 0; i < na; ++i) {
+      const ChainDesc& d = a.c[i];
+      int L = d.we - d.ws + 1;
+      const double* U = Lv.ubuf + d.uoff;
+      if (d.we + 1 < M.n) t1.push_back(make_task(M.H, M.ldh, 0, d.ws, d.we + 1, L, M.n - d.we - 1, U, kwin, nullptr));
+      if (M.Z) t1.push_back(make_task(M.Z, M.ldz, 1, 0, d.ws, L, M.zrows, U, kwin, nullptr));
+      if (d.ws > 0) t2.push_back(make_task(M.H, M.ldh, 1, 0, d.ws, L, d.ws, U, kwin, nullptr));
+    }
+    run_updates(t1);
+    run_updates(t2);
+  }
+  if (lev == 0) {
+    // algorithmic flops of applying the reflectors directly (12 flops per
+    // row/column entry of each 3x3 reflector): every bulge passes rows
+    // lo..hi; a reflector at row k touches n-k columns, k+4 rows and zrows
+    // rows of Z.
+    double m = hi - lo + 1;
+    double avgk = 0.5 * (lo + hi);
+    g_stats.reflector_flops += 12.0 * npairs * m * ((M.n - avgk) + (avgk + 4) + (M.Z ? M.zrows : 0));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The iteration of Sec. 2.1 on rows/cols ilo..ihi of M (full Schur form).
+// ---------------------------------------------------------------------------
+int Solver::qr_block(const Mat3& M, int lev, int ilo, int ihi) {
+  Level& Lv = levels[lev];
+  DeflParams dp = defl(M.n);
+  int kbot = ihi;
+  int itmax = 30 * std::max(10, ihi - ilo + 1);
+  int it = 0;
+  int ndfl = 1;
+  while (kbot >= ilo) {
+    k_scan<<<1, CTA_THREADS, 0, st>>>(M.H, M.ldh, ilo, kbot, dp, Lv.ctl);
+    ck(cudaGetLastError());
+    read_ctl(Lv.ctl);
+    int ktop = hctl->ktop;
+    int m = kbot - ktop + 1;
+    if (m == 1) {
+      kbot -= 1;
+      ndfl = 1;
+      continue;
+    }
+    if (m == 2) {
+      k_std2<<<1, CTA_THREADS, 0, st>>>(M.H, M.ldh, M.n, M.Z, M.ldz, M.Z ? M.zrows : 0, ktop);
+      ck(cudaGetLastError());
+      kbot -= 2;
+      ndfl = 1;
+      continue;
+    }
+    if (m <= opts.nmin) {
+      size_t smem = (size_t)(m | 1) * m * sizeof(double);
+      k_smallqr<<<1, CTA_THREADS, smem, st>>>(M.H, M.ldh, ktop, kbot, Lv.usmall, m, dp, Lv.ctl);
+      ck(cudaGetLastError());
+      apply_block_transform(M, ktop, m, Lv.usmall, m, nullptr);
+      read_ctl(Lv.ctl);
+      if (lev == 0) g_stats.small_qr += 1;
+      if (hctl->info) return hctl->info;
+      kbot = ktop - 1;
+      ndfl = 1;
+      continue;
+    }
+    ++it;
+    if (it > itmax) return kbot + 1;
+    int ns_max, nw;
+    default_ns_nw(m, &ns_max, &nw);
+    if (lev == 0) {
+      if (opts.n_shifts > 0) ns_max = opts.n_shifts;
+      if (opts.aed_window > 0) nw = opts.aed_window;
+    }
+    nw = std::min(std::min(std::min(nw, m), Lv.nwmax), 1024);
+    int nd = aed(M, lev, ktop, kbot, nw, ns_max, ndfl);
+    if (lev == 0) {
+      g_stats.aed_steps += 1;
+      g_stats.deflated_by_aed += nd;
+    }
+    kbot -= nd;
+    ndfl = hctl->ndfl;
+    int npairs = hctl->npairs;
+    m = kbot - ktop + 1;
+    if (m <= opts.nmin) continue;
+    if (nd > 0 && 100 * nd > opts.nibble * nw) continue;
+    if (npairs <= 0) continue;
+    sweep(M, lev, ktop, kbot, Lv.pairs, npairs, 0);
+    if (lev == 0) g_stats.sweeps += 1;
+  }
+  return 0;
+}
+
+// AED (Sec. 2.5) on the trailing nw x nw window of [ktop, kbot]; returns nd
+// and leaves the control block (npairs, ndfl, ncand) in hctl.
+int Solver::aed(const Mat3& M, int lev, int ktop, int kbot, int nw, int ns_max, int ndfl) {
+  Level& Lv = levels[lev];
+  DeflParams dp = defl(M.n);
+  DeflParams dpw = defl(nw);
+  int kwtop = kbot - nw + 1;
+  double* saved = cur_flops;
+  if (lev == 0) cur_flops = &g_stats.aed_gemm_flops;
+  if (nw <= NW_SMEM_MAX) {
+    size_t smem = (size_t)(nw | 1) * nw * sizeof(double);
+    k_aed_small<<<1, CTA_THREADS, smem, st>>>(M.H, M.ldh, ktop, kbot, nw, Lv.V, nw, Lv.cand_re, Lv.cand_im, Lv.vbuf,
+                                             dp, dpw, Lv.ctl);
+    ck(cudaGetLastError());
+  } else {
+    k_copy_window<<<std::min(nw, 4 * num_sms()), CTA_THREADS, 0, st>>>(M.H, M.ldh, kwtop, nw, Lv.T, nw, Lv.V, nw);
+    ck(cudaGetLastError());
+    Mat3 W{Lv.T, nw, nw, Lv.V, nw, nw};
+    double* keep = cur_flops;
+    cur_flops = nullptr;
+    int inner = qr_block(W, lev + 1, 0, nw - 1);
+    cur_flops = keep;
+    k_aed_big_post<<<1, CTA_THREADS, 0, st>>>(M.H, M.ldh, ktop, kbot, nw, Lv.T, nw, Lv.V, nw, Lv.cand_re, Lv.cand_im,
+                                              Lv.vbuf, dp, Lv.ctl, inner);
+    ck(cudaGetLastError());
+  }
+  apply_block_transform(M, kwtop, nw, Lv.V, nw, &Lv.ctl->nd);
+  k_make_pairs<<<1, 32, 0, st>>>(M.H, M.ldh, ktop, kbot, std::min(ns_max, Lv.nsmax + 8 - 4), ndfl, 6, Lv.cand_re,
+                                 Lv.cand_im, Lv.pairs, Lv.ctl);
+  ck(cudaGetLastError());
+  read_ctl(Lv.ctl);
+  cur_flops = saved;
+  return hctl->nd;
+}
+
+}  // namespace schur
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace schur;
+
+extern "C" int schur_default_opts(schur_opts* o) {
+  if (!o) return -1;
+  memset(o, 0, sizeof(*o));
+  o->struct_size = (int)sizeof(schur_opts);
+  o->nmin = 75;
+  o->nibble = 14;
+  o->deflation = SCHUR_DEFLATION_LAPACK;
+  o->want_z = 1;
+  o->z_init = 0;
+  return SCHUR_OK;
+}
+
+extern "C" const char* schur_status_string(int code) { return status_string(code); }
+
+extern "C" int schur_workspace_size(int n, const schur_opts* opts, size_t* bytes) {
+  if (n < 0) return -1;
+  if (!bytes) return -3;
+  schur_opts o;
+  schur_default_opts(&o);
+  if (opts) memcpy(&o, opts, std::min((size_t)std::max(opts->struct_size, 0), sizeof(o)));
+  *bytes = workspace_bytes(std::max(n, 1), o);
+  return SCHUR_OK;
+}
+
+extern "C" int schur_last_stats(schur_stats* out) {
+  if (!out) return -1;
+  *out = g_stats;
+  return SCHUR_OK;
+}
+
+static int frob_norm(const double* H, long long ldh, int n, cudaStream_t st, double* out);
+
+extern "C" int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, double* wr, double* wi,
+                                const schur_opts* opts) {
+  if (n < 0) return -1;
+  if (n > 0 && H == nullptr) return -2;
+  if (ldh < std::max(1, n)) return -3;
+  int want_z = opts ? opts->want_z : 1;
+  if (want_z && n > 0 && Z == nullptr) return -4;
+  if (want_z && ldz < std::max(1, n)) return -5;
+  if (n > 0 && wr == nullptr) return -6;
+  if (n > 0 && wi == nullptr) return -7;
+  memset(&g_stats, 0, sizeof(g_stats));
+  if (n == 0) return SCHUR_OK;
+  try {
+    Solver s(opts);
+    if (!s.opts.want_z) Z = nullptr;
+    int rc = s.setup(n);
+    if (rc) return rc;
+    ck(cudaMemsetAsync(s.flag, 0, sizeof(int), s.st));
+    int grid = std::min(n, 8 * num_sms());
+    k_prep<<<grid, CTA_THREADS, 0, s.st>>>(H, ldh, n, Z, ldz, s.opts.z_init, s.flag);
+    ck(cudaGetLastError());
+    int hflag = 0;
+    ck(cudaMemcpyAsync(&hflag, s.flag, sizeof(int), cudaMemcpyDeviceToHost, s.st));
+    ck(cudaStreamSynchronize(s.st));
+    if (hflag) return SCHUR_ERR_NONFINITE;
+    if (s.opts.deflation == SCHUR_DEFLATION_NORM) {
+      int r = frob_norm(H, ldh, n, s.st, &s.normH);
+      if (r) return r;
+    }
+    Mat3 M{H, ldh, n, Z, ldz, n};
+    s.cur_flops = &g_stats.sweep_gemm_flops;
+    int info = s.qr_block(M, 0, 0, n - 1);
+    k_extract_eigs<<<std::max(1, std::min((n + 255) / 256, 4 * num_sms())), 256, 0, s.st>>>(H, ldh, n, wr, wi);
+    ck(cudaGetLastError());
+    ck(cudaStreamSynchronize(s.st));
+    return info;
+  } catch (const CudaError&) {
+    return SCHUR_ERR_CUDA;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// ||H||_F of the Hessenberg part (norm-stable deflation, Sec. 5.6 item 2)
+// ---------------------------------------------------------------------------
+__global__ void k_frob(const double* H, long long ldh, int n, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int j = blockIdx.x; j < n; j += gridDim.x)
+    for (int i = threadIdx.x; i <= min(j + 1, n - 1); i += blockDim.x) {
+      double v = H[i + (long long)j * ldh];
+      s += v * v;
+    }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    atomicAdd(out, t);
+  }
+}
+
+static int frob_norm(const double* H, long long ldh, int n, cudaStream_t st, double* out) {
+  double* d = nullptr;
+  if (cudaMalloc((void**)&d, sizeof(double)) != cudaSuccess) return SCHUR_ERR_NOMEM;
+  cudaMemsetAsync(d, 0, sizeof(double), st);
+  k_frob<<<std::min(n, 4 * num_sms()), 256, 0, st>>>(H, ldh, n, d);
+  double h = 0.0;
+  cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return SCHUR_ERR_CUDA;
+  *out = sqrt(h);
+  return SCHUR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Single steps (parity tests)
+// ---------------------------------------------------------------------------
+extern "C" int schur_sweep(int n, double* H, int ldh, double* Z, int ldz, int ilo, int ihi, const double* pairs,
+                           int npairs, int bulges_per_chain, const schur_opts* opts) {
+  if (n < 1) return -1;
+  if (!H) return -2;
+  if (ldh < n) return -3;
+  if (Z && ldz < n) return -5;
+  if (ilo < 0 || ilo >= n) return -6;
+  if (ihi < ilo + 2 || ihi >= n) return -7;
+  if (!pairs) return -8;
+  if (npairs < 1 || npairs > MAX_CHAINS * MAX_BULGES_PER_CHAIN) return -9;
+  try {
+    Solver s(opts);
+    int rc = s.setup(n);
+    if (rc) return rc;
+    double* dpairs = nullptr;
+    ck(cudaMalloc((void**)&dpairs, 2 * npairs * sizeof(double)));
+    ck(cudaMemcpyAsync(dpairs, pairs, 2 * npairs * sizeof(double), cudaMemcpyHostToDevice, s.st));
+    Mat3 M{H, ldh, n, Z, ldz, n};
+    s.sweep(M, 0, ilo, ihi, dpairs, npairs, bulges_per_chain);
+    ck(cudaStreamSynchronize(s.st));
+    cudaFree(dpairs);
+    return SCHUR_OK;
+  } catch (const CudaError&) {
+    return SCHUR_ERR_CUDA;
+  }
+}
+
+extern "C" int schur_aed(int n, double* H, int ldh, double* Z, int ldz, int ktop, int kbot, int nw, int* nd,
+                         double* cand_re, double* cand_im, int* ncand, const schur_opts* opts) {
+  if (n < 1) return -1;
+  if (!H) return -2;
+  if (ldh < n) return -3;
+  if (Z && ldz < n) return -5;
+  if (ktop < 0 || ktop >= n) return -6;
+  if (kbot < ktop || kbot >= n) return -7;
+  if (nw < 1 || nw > kbot - ktop + 1) return -8;
+  if (!nd) return -9;
+  try {
+    schur_opts o;
+    schur_default_opts(&o);
+    if (opts) memcpy(&o, opts, std::min((size_t)std::max(opts->struct_size, 0), sizeof(o)));
+    o.aed_window = nw;
+    Solver s(&o);
+    int rc = s.setup(n);
+    if (rc) return rc;
+    if (s.opts.deflation == SCHUR_DEFLATION_NORM) {
+      int r = frob_norm(H, ldh, n, s.st, &s.normH);
+      if (r) return r;
+    }
+    Mat3 M{H, ldh, n, Z, ldz, n};
+    int d = s.aed(M, 0, ktop, kbot, nw, 8, 1);
+    *nd = d;
+    int nc = s.hctl->ncand;
+    if (ncand) *ncand = nc;
+    if (cand_re && nc > 0) ck(cudaMemcpy(cand_re, s.levels[0].cand_re, nc * sizeof(double), cudaMemcpyDeviceToHost));
+    if (cand_im && nc > 0) ck(cudaMemcpy(cand_im, s.levels[0].cand_im, nc * sizeof(double), cudaMemcpyDeviceToHost));
+    return SCHUR_OK;
+  } catch (const CudaError&) {
+    return SCHUR_ERR_CUDA;
+  }
+}
+
+extern "C" int schur_small_qr(int n, double* H, int ldh, double* Z, int ldz, int ilo, int ihi, const schur_opts* opts) {
+  if (n < 1) return -1;
+  if (!H) return -2;
+  if (ldh < n) return -3;
+  if (Z && ldz < n) return -5;
+  if (ilo < 0 || ilo >= n) return -6;
+  if (ihi < ilo || ihi >= n || ihi - ilo + 1 > NW_SMEM_MAX) return -7;
+  try {
+    Solver s(opts);
+    int rc = s.setup(n);
+    if (rc) return rc;
+    int m = ihi - ilo + 1;
+    Mat3 M{H, ldh, n, Z, ldz, n};
+    DeflParams dp = s.defl(n);
+    size_t smem = (size_t)(m | 1) * m * sizeof(double);
+    k_smallqr<<<1, CTA_THREADS, smem, s.st>>>(H, ldh, ilo, ihi, s.levels[0].usmall, m, dp, s.levels[0].ctl);
+    ck(cudaGetLastError());
+    s.apply_block_transform(M, ilo, m, s.levels[0].usmall, m, nullptr);
+    s.read_ctl(s.levels[0].ctl);
+    return s.hctl->info;
+  } catch (const CudaError&) {
+    return SCHUR_ERR_CUDA;
+  }
+}
+
+extern "C" int schur_apply_u(int side, double* A, int lda, int r0, int c0, int m, int k, const double* U, int ldu,
+                             const schur_opts* opts) {
+  if (side != 0 && side != 1) return -1;
+  if (!A) return -2;
+  if (lda < 1) return -3;
+  if (r0 < 0) return -4;
+  if (c0 < 0) return -5;
+  if (m < 0) return -6;
+  if (k < 1 || k > 1024) return -7;
+  if (!U) return -8;
+  if (ldu < k) return -9;
+  try {
+    Solver s(opts);
+    init_kernel_attributes();
+    std::vector<UpdTask> t;
+    t.push_back(make_task(A, lda, side, r0, c0, k, m, U, ldu, nullptr));
+    s.run_updates(t);
+    ck(cudaStreamSynchronize(s.st));
+    return SCHUR_OK;
+  } catch (const CudaError&) {
+    return SCHUR_ERR_CUDA;
+  }
+}

@@ -1,0 +1,75 @@
+// host.h -- host-side solver state shared by the C ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/schur_gb300.h"
+#include "common.cuh"
+
+#define KWIN_MAX 128   // largest bulge-chase window
+
+namespace schur {
+
+struct CudaError {
+  cudaError_t e;
+};
+
+// A matrix being reduced (full Schur form: every transform reaches all of H's
+// rows/columns and zrows rows of Z).
+struct Mat3 {
+  double* H;
+  long long ldh;
+  int n;
+  double* Z;
+  long long ldz;
+  int zrows;
+};
+
+// Device buffers of one recursion level (level 0 = the input matrix, level 1
+// = an AED window reduced by the same iteration).
+struct Level {
+  int n = 0, nwmax = 0, nsmax = 0;
+  Ctl* ctl = nullptr;
+  double* ubuf = nullptr;
+  double* V = nullptr;
+  double* T = nullptr;
+  double* cand_re = nullptr;
+  double* cand_im = nullptr;
+  double* pairs = nullptr;
+  double* vbuf = nullptr;
+  double* usmall = nullptr;
+};
+
+struct Solver {
+  schur_opts opts;
+  cudaStream_t st = nullptr;
+  Ctl* hctl = nullptr;       // pinned mirror of the control block
+  char* owned = nullptr;     // scratch allocated by the library
+  int* flag = nullptr;
+  double normH = 0.0;
+  double* cur_flops = nullptr;
+  std::vector<Level> levels;
+
+  explicit Solver(const schur_opts* o);
+  ~Solver();
+  int setup(int n);
+  void carve(char* base, int n);
+  void read_ctl(const Ctl* d);
+  DeflParams defl(int n) const;
+  void run_updates(std::vector<UpdTask>& tasks);
+  void apply_block_transform(const Mat3& M, int k0, int L, const double* U, int ldu, const int* gate);
+  void sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs, int npairs, int nbc_req);
+  int qr_block(const Mat3& M, int lev, int ilo, int ihi);
+  int aed(const Mat3& M, int lev, int ktop, int kbot, int nw, int ns_max, int ndfl);
+};
+
+extern thread_local schur_stats g_stats;
+void init_kernel_attributes();
+int num_sms();
+void default_ns_nw(int m, int* ns, int* nw);
+size_t workspace_bytes(int n, const schur_opts& o);
+const char* status_string(int code);
+
+}  // namespace schur

@@ -1,0 +1,528 @@
+// kernels.cu -- device kernels of the single-matrix path.
+//
+//   k_prep          input check (finite), zero below the subdiagonal, Z = I
+//   k_scan          vigilant-deflation scan of the subdiagonal (Sec. 2.1)
+//   k_std2          standardise a decoupled 2x2 block (eq. 2by2_blocks)
+//   k_smallqr       double-shift QR of a small block in shared memory,
+//                   transform accumulated into U (Sec. 2.2, "small Schur")
+//   k_aed_small     whole AED step for windows <= NW_SMEM_MAX (Sec. 2.5)
+//   k_copy_window / k_aed_big_post
+//                   AED for larger windows: copy out, (recursive QR on the
+//                   host-driven path), then deflation checks, reordering and
+//                   spike elimination on the window in global memory
+//   k_make_pairs    next sweep's shift pairs from the AED candidates
+//                   (or exceptional shifts)
+//   k_chase         windowed bulge chase of several chains (Sec. 2.3, 2.4),
+//                   window and accumulator U in shared memory
+//   k_apply_u       off-window products U^T X / X U (Sec. 3.2.1), FP64 FFMA
+//   k_extract_eigs  eigenvalues from the standardised diagonal blocks
+#include "cta.cuh"
+#include "kernels.cuh"
+
+// ---------------------------------------------------------------------------
+__global__ void k_set_int(int* p, int v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
+__global__ void k_prep(double* H, long long ldh, int n, double* Z, long long ldz, int zinit, int* nonfinite) {
+  for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    double* col = H + (long long)j * ldh;
+    int bad = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (i > j + 1)
+        col[i] = 0.0;
+      else if (!isfinite(col[i]))
+        bad = 1;
+    }
+    if (bad) atomicOr(nonfinite, 1);
+    if (Z != nullptr && zinit == 0) {
+      double* zc = Z + (long long)j * ldz;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) zc[i] = (i == j) ? 1.0 : 0.0;
+    }
+  }
+}
+
+__global__ void k_scan(double* H, long long ldh, int lo, int hi, DeflParams dp, Ctl* ctl) {
+  __shared__ CtaShared sh;
+  Mat Hm{H, ldh};
+  int l = cta_find_ktop(Hm, lo, hi, dp, &sh);
+  if (threadIdx.x == 0) ctl->ktop = l;
+}
+
+__global__ void k_std2(double* H, long long ldh, int n, double* Z, long long ldz, int zrows, int k) {
+  __shared__ CtaShared sh;
+  Mat Hm{H, ldh};
+  Mat Zm{Z, ldz};
+  cta_standardize_block(Hm, k, n, Zm, zrows, &sh);
+}
+
+// ---------------------------------------------------------------------------
+// Small block [ilo, ihi] (m <= NW_SMEM_MAX): copy to shared memory, Francis
+// QR with the transform accumulated into U (m x m, global), copy back.  The
+// off-window rows/columns and Z are updated afterwards by k_apply_u.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(CTA_THREADS) k_smallqr(double* H, long long ldh, int ilo, int ihi, double* U,
+                                                         int ldu, DeflParams dp, Ctl* ctl) {
+  extern __shared__ double smem[];
+  __shared__ CtaShared sh;
+  int m = ihi - ilo + 1;
+  int ldt = m | 1;
+  Mat T{smem, ldt};
+  Mat Um{U, ldu};
+  for (int j = 0; j < m; ++j)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      T(i, j) = (i <= j + 1) ? H[(ilo + i) + (long long)(ilo + j) * ldh] : 0.0;
+      Um(i, j) = (i == j) ? 1.0 : 0.0;
+    }
+  __syncthreads();
+  int info = cta_francis(T, m, 0, m - 1, Um, m, dp, &sh);
+  for (int j = 0; j < m; ++j)
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+      H[(ilo + i) + (long long)(ilo + j) * ldh] = (i <= j + 1) ? T(i, j) : 0.0;
+  if (threadIdx.x == 0) ctl->info = info ? (ilo + info) : 0;
+}
+
+// ---------------------------------------------------------------------------
+// AED on the trailing window [kwtop, kbot] of the active block [ktop, kbot]
+// with the window held in shared memory.
+// ---------------------------------------------------------------------------
+__device__ void aed_write_back(double* H, long long ldh, int ktop, int kwtop, int nw, const Mat& T, double top) {
+  for (int j = 0; j < nw; ++j)
+    for (int i = threadIdx.x; i < nw; i += blockDim.x)
+      H[(kwtop + i) + (long long)(kwtop + j) * ldh] = (i <= j + 1) ? T(i, j) : 0.0;
+  if (kwtop > ktop) {
+    for (int i = threadIdx.x; i < nw; i += blockDim.x)
+      H[(kwtop + i) + (long long)(kwtop - 1) * ldh] = (i == 0) ? top : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(CTA_THREADS) k_aed_small(double* H, long long ldh, int ktop, int kbot, int nw,
+                                                           double* V, int ldv, double* cand_re, double* cand_im,
+                                                           double* vbuf, DeflParams dp, DeflParams dpw, Ctl* ctl) {
+  extern __shared__ double smem[];
+  __shared__ CtaShared sh;
+  __shared__ int s_ncand, s_swf;
+  int kwtop = kbot - nw + 1;
+  int ldt = nw | 1;
+  Mat T{smem, ldt};
+  Mat Vm{V, ldv};
+  for (int j = 0; j < nw; ++j)
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) {
+      T(i, j) = (i <= j + 1) ? H[(kwtop + i) + (long long)(kwtop + j) * ldh] : 0.0;
+      Vm(i, j) = (i == j) ? 1.0 : 0.0;
+    }
+  double s = (kwtop > ktop) ? H[kwtop + (long long)(kwtop - 1) * ldh] : 0.0;
+  __syncthreads();
+  int info = cta_francis(T, nw, 0, nw - 1, Vm, nw, dpw, &sh);
+  double top;
+  int nd = cta_aed_post(T, nw, info, s, Vm, dp, vbuf, cand_re, cand_im, &s_ncand, &top, &s_swf, &sh);
+  if (nd > 0) aed_write_back(H, ldh, ktop, kwtop, nw, T, top);
+  if (threadIdx.x == 0) {
+    ctl->nd = nd;
+    ctl->ncand = s_ncand;
+    ctl->swap_fail = s_swf;
+  }
+}
+
+__global__ void k_copy_window(const double* H, long long ldh, int kwtop, int nw, double* T, int ldt, double* V,
+                              int ldv) {
+  for (int j = blockIdx.x; j < nw; j += gridDim.x)
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) {
+      T[i + (long long)j * ldt] = (i <= j + 1) ? H[(kwtop + i) + (long long)(kwtop + j) * ldh] : 0.0;
+      V[i + (long long)j * ldv] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+// AED steps 2-3 for a window whose Schur form T (global, with transform V)
+// was computed by the recursive driver; inner_info = its return code
+// (rows 0..inner_info-1 unreduced).
+__global__ void __launch_bounds__(CTA_THREADS) k_aed_big_post(double* H, long long ldh, int ktop, int kbot, int nw,
+                                                              double* T, int ldt, double* V, int ldv,
+                                                              double* cand_re, double* cand_im, double* vbuf,
+                                                              DeflParams dp, Ctl* ctl, int inner_info) {
+  __shared__ CtaShared sh;
+  __shared__ int s_ncand, s_swf;
+  int kwtop = kbot - nw + 1;
+  Mat Tm{T, ldt};
+  Mat Vm{V, ldv};
+  int info = inner_info;
+  double s = (kwtop > ktop) ? H[kwtop + (long long)(kwtop - 1) * ldh] : 0.0;
+  double top;
+  int nd = cta_aed_post(Tm, nw, info, s, Vm, dp, vbuf, cand_re, cand_im, &s_ncand, &top, &s_swf, &sh);
+  __syncthreads();
+  if (nd > 0) aed_write_back(H, ldh, ktop, kwtop, nw, Tm, top);
+  if (threadIdx.x == 0) {
+    ctl->nd = nd;
+    ctl->ncand = s_ncand;
+    ctl->swap_fail = s_swf;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shift pairs for the next sweep (one thread).  Reading of Sec. 2.5: the
+// undeflated AED candidates become the shifts -- the bottom-most ones, complex
+// conjugates kept together, real shifts paired in order of appearance; an
+// exceptional pair every exc_period-th iteration without deflation; the
+// trailing 2x2 when no candidate is left.
+// ---------------------------------------------------------------------------
+__global__ void k_make_pairs(const double* H, long long ldh, int ktop, int kbot_old, int ns_max, int ndfl_host,
+                             int exc_period, const double* cand_re, const double* cand_im, double* pairs, Ctl* ctl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Mat Hm{const_cast<double*>(H), ldh};
+  int nd = ctl->nd;
+  int kbot = kbot_old - nd;
+  int m = kbot - ktop + 1;
+  int ndfl = (nd > 0) ? 1 : ndfl_host + 1;
+  int ns = min(ns_max, m - 1);
+  ns -= ns % 2;
+  int want = ns / 2;
+  int np = 0;
+  if (m >= 3 && want > 0) {
+    if (ndfl % exc_period == 0) {
+      for (int i = kbot; np < want && i > ktop; i -= 2) {
+        double ss, sp;
+        exceptional_pair(Hm, ktop, i, ss, sp);
+        pairs[2 * np] = ss;
+        pairs[2 * np + 1] = sp;
+        ++np;
+      }
+    } else {
+      int nc = ctl->ncand;
+      bool pending = false;
+      double pv = 0.0;
+      int i = nc - 1;
+      while (i >= 0 && np < want) {
+        double re = cand_re[i], im = cand_im[i];
+        if (im != 0.0) {
+          pairs[2 * np] = 2.0 * re;
+          pairs[2 * np + 1] = re * re + im * im;
+          ++np;
+          i -= 2;
+          continue;
+        }
+        if (!pending) {
+          pending = true;
+          pv = re;
+        } else {
+          pairs[2 * np] = pv + re;
+          pairs[2 * np + 1] = pv * re;
+          ++np;
+          pending = false;
+        }
+        i -= 1;
+      }
+      if (np == 0) {
+        double a = Hm(kbot - 1, kbot - 1), b = Hm(kbot - 1, kbot), c = Hm(kbot, kbot - 1), d = Hm(kbot, kbot);
+        pairs[0] = a + d;
+        pairs[1] = a * d - b * c;
+        np = 1;
+      }
+    }
+  }
+  ctl->npairs = np;
+  ctl->ndfl = ndfl;
+}
+
+// ---------------------------------------------------------------------------
+// Windowed bulge chase (Sec. 2.3, Fig. 2; several chains as in Fig. 3).
+//
+// Block c moves chain c through its window [ws, we]: chain-local steps
+// tau0..tau1-1, bulge j of the chain at row k = lo + tau - 3 j.  Per step:
+// (A) every bulge's reflector is built from the window (the shift vector at
+// k = lo, else column k-1), (B) all left products on the in-window columns,
+// (C) all right products on the in-window rows and on the accumulator U.
+// Doing the bulges of a step bottom-first in this three-phase order gives the
+// reflectors of introducing the bulges one at a time and chasing each just far
+// enough (different bulges touch disjoint rows/columns except where a left
+// and a right product meet, and those commute).  The window and U are then
+// written back; k_apply_u applies U off-window.
+// ---------------------------------------------------------------------------
+size_t chase_smem_bytes(int kwin) {
+  size_t ld = (size_t)(kwin | 1);
+  return 2 * ld * (size_t)kwin * sizeof(double);
+}
+
+__global__ void __launch_bounds__(CTA_THREADS) k_chase(double* H, long long ldh, const double* pairs, double* Ubuf,
+                                                       const __grid_constant__ ChaseArgs args) {
+  extern __shared__ double smem[];
+  __shared__ double rv1[MAX_BULGES_PER_CHAIN], rv2[MAX_BULGES_PER_CHAIN], rtau[MAX_BULGES_PER_CHAIN];
+  __shared__ int rk[MAX_BULGES_PER_CHAIN], rnr[MAX_BULGES_PER_CHAIN];
+  const ChainDesc& d = args.c[blockIdx.x];
+  const int ws = d.ws;
+  const int L = d.we - d.ws + 1;
+  const int ld = L | 1;
+  Mat W{smem, ld};
+  Mat Us{smem + (size_t)ld * L, ld};
+  const int lo = args.lo, hi = args.hi;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = 0; j < L; ++j)
+    for (int i = tid; i < L; i += nt) {
+      W(i, j) = H[(ws + i) + (long long)(ws + j) * ldh];
+      Us(i, j) = (i == j) ? 1.0 : 0.0;
+    }
+  __syncthreads();
+  const int nb = d.nb;
+  const int hil = hi - ws;  // local index of hi
+  for (int tau = d.tau0; tau < d.tau1; ++tau) {
+    // (A) reflectors
+    if (tid < nb) {
+      int j = tid;
+      int k = lo + tau - 3 * j;
+      if (k >= lo && k <= hi - 1) {
+        int nr = min(3, hi - k + 1);
+        int kl = k - ws;
+        double x0, x1, x2 = 0.0;
+        if (k == lo) {
+          double ssum = pairs[2 * (d.pair0 + j)], sprod = pairs[2 * (d.pair0 + j) + 1];
+          double h00 = W(kl, kl), h01 = W(kl, kl + 1), h10 = W(kl + 1, kl), h11 = W(kl + 1, kl + 1);
+          x0 = h00 * h00 + h01 * h10 - ssum * h00 + sprod;
+          x1 = h10 * (h00 + h11 - ssum);
+          if (nr == 3) x2 = h10 * W(kl + 2, kl + 1);
+        } else {
+          x0 = W(kl, kl - 1);
+          x1 = W(kl + 1, kl - 1);
+          if (nr == 3) x2 = W(kl + 2, kl - 1);
+        }
+        double v1, v2, t, beta;
+        house3(nr, x0, x1, x2, v1, v2, t, beta);
+        if (k > lo) {
+          W(kl, kl - 1) = beta;
+          W(kl + 1, kl - 1) = 0.0;
+          if (nr == 3) W(kl + 2, kl - 1) = 0.0;
+        }
+        rv1[j] = v1;
+        rv2[j] = v2;
+        rtau[j] = t;
+        rk[j] = kl;
+        rnr[j] = nr;
+      } else {
+        rnr[j] = 0;
+      }
+    }
+    __syncthreads();
+    // (B) left products: bulge j on rows kl..kl+nr-1, in-window columns kl..L-1
+    {
+      int base = 0;
+      for (int j = 0; j < nb; ++j) {
+        int nr = rnr[j];
+        if (nr == 0) continue;
+        int kl = rk[j];
+        int cnt = L - kl;
+        double v1 = rv1[j], v2 = rv2[j], t = rtau[j];
+        int start = (tid - base) % nt;
+        if (start < 0) start += nt;
+        for (int c = start; c < cnt; c += nt) {
+          double* col = &W(kl, kl + c);
+          double a0 = col[0], a1 = col[1], a2 = (nr == 3) ? col[2] : 0.0;
+          double s = t * (a0 + v1 * a1 + v2 * a2);
+          col[0] = a0 - s;
+          col[1] = a1 - s * v1;
+          if (nr == 3) col[2] = a2 - s * v2;
+        }
+        base += cnt;
+      }
+    }
+    __syncthreads();
+    // (C) right products: bulge j on columns kl..kl+nr-1, window rows
+    // 0..min(kl+3, hil), and on all L rows of U
+    {
+      int base = 0;
+      for (int j = 0; j < nb; ++j) {
+        int nr = rnr[j];
+        if (nr == 0) continue;
+        int kl = rk[j];
+        double v1 = rv1[j], v2 = rv2[j], t = rtau[j];
+        int rmax = min(kl + 3, hil);
+        int cnt = rmax + 1;
+        int start = (tid - base) % nt;
+        if (start < 0) start += nt;
+        double* c0 = &W(0, kl);
+        for (int r = start; r < cnt; r += nt) {
+          double a0 = c0[r], a1 = c0[r + ld], a2 = (nr == 3) ? c0[r + 2 * ld] : 0.0;
+          double s = t * (a0 + v1 * a1 + v2 * a2);
+          c0[r] = a0 - s;
+          c0[r + ld] = a1 - s * v1;
+          if (nr == 3) c0[r + 2 * ld] = a2 - s * v2;
+        }
+        base += cnt;
+        start = (tid - base) % nt;
+        if (start < 0) start += nt;
+        double* u0 = &Us(0, kl);
+        for (int r = start; r < L; r += nt) {
+          double a0 = u0[r], a1 = u0[r + ld], a2 = (nr == 3) ? u0[r + 2 * ld] : 0.0;
+          double s = t * (a0 + v1 * a1 + v2 * a2);
+          u0[r] = a0 - s;
+          u0[r + ld] = a1 - s * v1;
+          if (nr == 3) u0[r + 2 * ld] = a2 - s * v2;
+        }
+        base += L;
+      }
+    }
+    __syncthreads();
+  }
+  double* Uout = Ubuf + d.uoff;
+  for (int j = 0; j < L; ++j)
+    for (int i = tid; i < L; i += nt) {
+      H[(ws + i) + (long long)(ws + j) * ldh] = W(i, j);
+      Uout[i + (long long)j * args.ldu] = Us(i, j);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Off-window products (Sec. 3.2.1 left/right update), FP64 FFMA.
+//
+// A tile is TN vectors of one task, all L entries each, so a block owns its
+// output and updates A in place.  y = U^T x for every vector x (a column of X
+// for side 0; a row of X for side 1, where X U = (U^T X^T)^T).  U streams
+// through shared memory in chunks of KC rows; each thread keeps RM x 4
+// accumulators (rows rg + RG*t, vectors 4*vg .. 4*vg+3).
+// ---------------------------------------------------------------------------
+int apply_u_tn(int maxL) {
+  if (maxL <= 128) return 64;
+  if (maxL <= 256) return 32;
+  if (maxL <= 512) return 16;
+  return 8;
+}
+
+__host__ __device__ static inline int apply_u_kc(int L) {
+  int kc = 16384 / (L + 1);
+  return kc < L ? (kc < 1 ? 1 : kc) : L;
+}
+
+size_t apply_u_smem_bytes(int tn, int maxL) {
+  size_t ldv = (size_t)tn + 1;
+  size_t kc = (size_t)apply_u_kc(maxL);
+  return ((size_t)maxL * ldv + kc * ((size_t)maxL + 1)) * sizeof(double);
+}
+
+template <int TN>
+__global__ void __launch_bounds__(CTA_THREADS) k_apply_u(const __grid_constant__ UpdArgs args) {
+  extern __shared__ double smem[];
+  constexpr int CN = 4;
+  constexpr int VG = TN / CN;          // vector groups
+  constexpr int RG = CTA_THREADS / VG; // row groups
+  constexpr int LDV = TN + 1;
+  const int tid = threadIdx.x;
+  const int vg = tid % VG, rg = tid / VG;
+  const UpdTask& last = args.t[args.ntask - 1];
+  const int total = last.tile0 + last.ntile;
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    int ti = 0;
+    while (ti + 1 < args.ntask && args.t[ti + 1].tile0 <= tile) ++ti;
+    const UpdTask& t = args.t[ti];
+    if (t.gate != nullptr && *t.gate == 0) continue;
+    const int L = t.L;
+    const int v0 = (tile - t.tile0) * TN;
+    const int nv = min(TN, t.nvec - v0);
+    const int RM = (L + RG - 1) / RG;
+    const int KC = apply_u_kc(L);
+    const int LDU = L + 1;
+    double* sX = smem;                       // [L][LDV]: sX[k*LDV + v]
+    double* sU = smem + (size_t)L * LDV;     // [KC][LDU]: sU[kk*LDU + i]
+    const long long lda = t.lda;
+    // load the TN vectors
+    if (t.side == 0) {
+      for (int idx = tid; idx < L * TN; idx += CTA_THREADS) {
+        int k = idx % L, v = idx / L;
+        sX[k * LDV + v] = (v < nv) ? t.A[(t.r0 + k) + (long long)(t.c0 + v0 + v) * lda] : 0.0;
+      }
+    } else {
+      for (int idx = tid; idx < L * TN; idx += CTA_THREADS) {
+        int v = idx % TN, k = idx / TN;
+        sX[k * LDV + v] = (v < nv) ? t.A[(t.r0 + v0 + v) + (long long)(t.c0 + k) * lda] : 0.0;
+      }
+    }
+    double acc[8][CN];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int c = 0; c < CN; ++c) acc[a][c] = 0.0;
+    for (int kc = 0; kc < L; kc += KC) {
+      const int kn = min(KC, L - kc);
+      __syncthreads();
+      for (int idx = tid; idx < kn * L; idx += CTA_THREADS) {
+        int kk = idx % kn, i = idx / kn;
+        sU[kk * LDU + i] = t.U[(kc + kk) + (long long)i * t.ldu];
+      }
+      __syncthreads();
+      for (int kk = 0; kk < kn; ++kk) {
+        const double* xr = sX + (size_t)(kc + kk) * LDV + vg * CN;
+        double xv[CN];
+#pragma unroll
+        for (int c = 0; c < CN; ++c) xv[c] = xr[c];
+        const double* ur = sU + (size_t)kk * LDU;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          if (a < RM) {
+            int i = rg + RG * a;
+            double u = (i < L) ? ur[i] : 0.0;
+#pragma unroll
+            for (int c = 0; c < CN; ++c) acc[a][c] = fma(u, xv[c], acc[a][c]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // stage the outputs (i-major) and store
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      if (a < RM) {
+        int i = rg + RG * a;
+        if (i < L) {
+#pragma unroll
+          for (int c = 0; c < CN; ++c) sX[i * LDV + vg * CN + c] = acc[a][c];
+        }
+      }
+    }
+    __syncthreads();
+    if (t.side == 0) {
+      for (int idx = tid; idx < L * TN; idx += CTA_THREADS) {
+        int k = idx % L, v = idx / L;
+        if (v < nv) t.A[(t.r0 + k) + (long long)(t.c0 + v0 + v) * lda] = sX[k * LDV + v];
+      }
+    } else {
+      for (int idx = tid; idx < L * TN; idx += CTA_THREADS) {
+        int v = idx % TN, k = idx / TN;
+        if (v < nv) t.A[(t.r0 + v0 + v) + (long long)(t.c0 + k) * lda] = sX[k * LDV + v];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_apply_u(int tn, int grid, size_t smem, cudaStream_t st, const UpdArgs& a) {
+  switch (tn) {
+    case 64: k_apply_u<64><<<grid, CTA_THREADS, smem, st>>>(a); break;
+    case 32: k_apply_u<32><<<grid, CTA_THREADS, smem, st>>>(a); break;
+    case 16: k_apply_u<16><<<grid, CTA_THREADS, smem, st>>>(a); break;
+    default: k_apply_u<8><<<grid, CTA_THREADS, smem, st>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t apply_u_set_smem(int bytes) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_apply_u<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+  if ((e = cudaFuncSetAttribute(k_apply_u<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+  if ((e = cudaFuncSetAttribute(k_apply_u<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+  return cudaFuncSetAttribute(k_apply_u<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_extract_eigs(const double* H, long long ldh, int n, double* wr, double* wi) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int s = -1;
+    if (j + 1 < n && H[(j + 1) + (long long)j * ldh] != 0.0) s = j;
+    else if (j > 0 && H[j + (long long)(j - 1) * ldh] != 0.0) s = j - 1;
+    if (s < 0) {
+      wr[j] = H[j + (long long)j * ldh];
+      wi[j] = 0.0;
+    } else {
+      double r1, i1, r2, i2;
+      eig2x2(H[s + (long long)s * ldh], H[s + (long long)(s + 1) * ldh], H[(s + 1) + (long long)s * ldh],
+             H[(s + 1) + (long long)(s + 1) * ldh], r1, i1, r2, i2);
+      wr[j] = (j == s) ? r1 : r2;
+      wi[j] = (j == s) ? i1 : i2;
+    }
+  }
+}

@@ -1,0 +1,278 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances.  The Schur form is not unique (block order, signs), so whole runs
+are compared on invariants: backward error ||H - Z S Z^T||_F / ||H||_F,
+orthogonality ||Z^T Z - I||_F / sqrt(n) (both <= 1e-13, the paper's metrics
+of Sec. 5.4 at ~450 u), the standardised quasi-triangular structure, and
+eigenvalues matched one-to-one within 1e-10 * kappa_i * ||H||_F (kappa_i the
+condition number of eigenvalue i from the oracle's Schur factor).  Single
+steps fed identical inputs (one sweep with fixed shifts, one product) are
+compared entrywise: the same reflectors, only grouped differently, so the
+difference is rounding, bounded here by 1e-11 * ||H||_F.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import householder, qr, metrics, testmats  # noqa: E402
+from paper_2007_03576_gb300 import api, inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+U = qr.U
+
+
+def _dev(A):
+    """numpy (row-major math layout) -> column-major CUDA tensor."""
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.float64).T)).cuda().t()
+
+
+def _np(T):
+    return T.detach().cpu().numpy()
+
+
+def _eig_match(lam, ref, S_ref, nH, tol=1e-10):
+    _, kap = metrics.eig_condition(S_ref)
+    perm, dist = metrics.match_eigenvalues(np.asarray(ref), np.asarray(lam))
+    bound = tol * kap * nH
+    assert np.all(dist <= bound), float(np.max(dist / (kap * nH)))
+    return float(np.max(dist / (kap * nH)))
+
+
+def _check_result(H, S, Z, tol=1e-13, block=None):
+    n = H.shape[0]
+    ra = np.linalg.norm(Z @ S @ Z.T - H) / np.linalg.norm(H)
+    ro = np.linalg.norm(Z.T @ Z - np.eye(n)) / math.sqrt(n)
+    assert ra <= tol, ra
+    assert ro <= tol, ro
+    blk = slice(None) if block is None else block
+    assert metrics.schur_structure_errors(S[blk, blk]) == []
+    return ra, ro
+
+
+# ----------------------------------------------------------------- products
+
+
+@pytest.mark.parametrize("k,m", [(7, 33), (48, 200), (96, 1000), (128, 257), (300, 77), (600, 130)])
+@pytest.mark.parametrize("side", [0, 1])
+def test_apply_u_matches_product(k, m, side):
+    """Off-window product (Sec. 3.2.1) vs a float64 numpy product; error
+    within k u ||U|| ||X|| (P8)."""
+    rng = np.random.default_rng(k * 7 + m + side)
+    n = max(k, m) + 20
+    A = rng.standard_normal((n, n))
+    Uq, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    r0, c0 = 3, 5
+    Ad = _dev(A)
+    api.apply_u(side, Ad, r0, c0, m, _dev(Uq))
+    got = _np(Ad)
+    ref = A.copy()
+    if side == 0:
+        ref[r0:r0 + k, c0:c0 + m] = Uq.T @ A[r0:r0 + k, c0:c0 + m]
+    else:
+        ref[r0:r0 + m, c0:c0 + k] = A[r0:r0 + m, c0:c0 + k] @ Uq
+    err = np.max(np.abs(got - ref))
+    assert err <= 4 * k * U * np.sqrt(k) * np.max(np.abs(A)), err
+
+
+# ----------------------------------------------------------------- sweeps
+
+
+@pytest.mark.parametrize("n,lo,hi,npairs,nbc", [
+    (40, 0, 39, 1, 1),
+    (64, 0, 63, 4, 4),
+    (120, 0, 119, 8, 2),
+    (200, 10, 180, 12, 4),
+    (300, 0, 299, 16, 16),
+    (500, 50, 499, 24, 6),
+])
+def test_sweep_matches_oracle(n, lo, hi, npairs, nbc):
+    """Windowed multi-chain bulge chase (Sec. 2.3/2.4) vs the oracle's direct
+    pipelined sweep with the same shift pairs: entrywise equal H and Z up to
+    rounding (P7)."""
+    rng = np.random.default_rng(n + npairs)
+    H = inputs.hessrand(n, 1000 + n)
+    if lo > 0:
+        H[lo, lo - 1] = 0.0
+    if hi < n - 1:
+        H[hi + 1, hi] = 0.0
+    pairs = []
+    for b in range(npairs):
+        if b % 2 == 0:
+            re, im = rng.uniform(-3, 3), rng.uniform(0.5, 3)
+            pairs.append((2 * re, re * re + im * im))
+        else:
+            a, c = rng.uniform(-3, 3, 2)
+            pairs.append((a + c, a * c))
+    Ho, Zo = H.copy(), np.eye(n)
+    qr.multishift_sweep(Ho, Zo, lo, hi, pairs)
+    Hd, Zd = _dev(H), _dev(np.eye(n))
+    api.sweep(Hd, Zd, lo, hi, pairs, bulges_per_chain=nbc)
+    Hg, Zg = _np(Hd), _np(Zd)
+    nh = np.linalg.norm(H)
+    assert np.max(np.abs(Hg - Ho)) <= 1e-11 * nh, np.max(np.abs(Hg - Ho)) / nh
+    assert np.max(np.abs(Zg - Zo)) <= 1e-11, np.max(np.abs(Zg - Zo))
+    assert np.max(np.abs(np.tril(Hg, -2))) == 0.0
+
+
+# ----------------------------------------------------------------- small QR
+
+
+@pytest.mark.parametrize("n,lo,hi", [(30, 0, 29), (80, 5, 74), (160, 0, 159)])
+def test_small_qr_matches_oracle(n, lo, hi):
+    """One-block double-shift QR (Sec. 2.2) vs the oracle's francis_qr on the
+    same block: invariants, and the eigenvalues of the block."""
+    H = inputs.hessrand(n, 2000 + n)
+    if lo > 0:
+        H[lo, lo - 1] = 0.0
+    if hi < n - 1:
+        H[hi + 1, hi] = 0.0
+    Ho, Zo = H.copy(), np.eye(n)
+    P = qr.Params(normH=np.linalg.norm(H))
+    assert qr.francis_qr(Ho, Zo, lo, hi, P) == 0
+    Hd, Zd = _dev(H), _dev(np.eye(n))
+    assert api.small_qr(Hd, Zd, lo, hi) == 0
+    Hg, Zg = _np(Hd), _np(Zd)
+    blk = slice(lo, hi + 1)
+    _check_result(H, Hg, Zg, block=blk)
+    lam_g = np.array([complex(*e) for e in qr.block_eigs(Hg, lo, hi + 1)])
+    lam_o = np.array([complex(*e) for e in qr.block_eigs(Ho, lo, hi + 1)])
+    _eig_match(lam_g, lam_o, Ho[blk, blk], np.linalg.norm(H))
+
+
+# ----------------------------------------------------------------- AED
+
+
+@pytest.mark.parametrize("n,nw,pre", [(60, 20, 2), (200, 48, 3), (300, 160, 4), (400, 200, 4)])
+def test_aed_matches_oracle(n, nw, pre):
+    """One AED step (Sec. 2.5) on identical inputs: the same number of
+    deflations and the same candidate multiset (to rounding), orthogonal
+    similarity, Hessenberg form restored.  nw = 200 exercises the recursive
+    window path (window reduced by the multishift driver itself)."""
+    H = inputs.hessrand(n, 3000 + n)
+    Z = np.eye(n)
+    for _ in range(pre):  # let the bottom converge a little
+        qr.multishift_sweep(H, Z, 0, n - 1, [(0.0, 1.0), (1.0, 2.0), (-1.0, 3.0)])
+    P = qr.Params(normH=np.linalg.norm(H))
+    Ho, Zo = H.copy(), np.eye(n)
+    nd_o, cand_o = qr.aed(Ho, Zo, 0, n - 1, nw, P)
+    Hd, Zd = _dev(H), _dev(np.eye(n))
+    nd_g, cand_g = api.aed(Hd, Zd, 0, n - 1, nw)
+    Hg, Zg = _np(Hd), _np(Zd)
+    assert nd_g == nd_o
+    assert len(cand_g) == len(cand_o)
+    if cand_o:
+        perm, dist = metrics.match_eigenvalues(np.array([complex(*c) for c in cand_o]), np.array(cand_g))
+        assert np.max(dist) <= 1e-8 * np.linalg.norm(H)
+    assert np.linalg.norm(Zg @ Hg @ Zg.T - H) <= 1e-13 * np.linalg.norm(H) * 10
+    assert np.max(np.abs(np.tril(Hg, -2))) == 0.0
+    assert np.linalg.norm(Zg.T @ Zg - np.eye(n)) / math.sqrt(n) < 1e-13
+
+
+# ----------------------------------------------------------------- end to end
+
+
+@pytest.mark.parametrize("n,seed,kw", [
+    (1, 0, {}), (2, 1, {}), (3, 2, {}), (17, 3, {}), (76, 4, {}), (100, 5, {}), (333, 7, {}),
+])
+def test_schur_hessrand_vs_oracle(n, seed, kw):
+    H = inputs.hessrand(n, 4000 + seed)
+    S, Z, wr, wi, info = api.schur(_dev(H), **kw)
+    assert info == 0
+    Sg, Zg = _np(S), _np(Z)
+    if n > 1:
+        _check_result(H, Sg, Zg)
+    So, Zo, wro, wio, info_o = qr.schur(H)
+    lam = _np(wr) + 1j * _np(wi)
+    _eig_match(lam, wro + 1j * wio, So, np.linalg.norm(H))
+    # wr/wi agree with S's diagonal blocks
+    wr2, wi2 = qr.eig_from_schur(Sg)
+    assert np.array_equal(wr2, _np(wr)) or np.allclose(wr2, _np(wr), rtol=0, atol=1e-14 * np.linalg.norm(H))
+
+
+def test_schur_workload_n256():
+    """The n = 256 workload: a seeded dense N(0,1) matrix reduced to
+    Hessenberg form by the oracle's Householder reduction; 8 shifts, AED
+    window 32, Z accumulated (starting from the reduction's Q)."""
+    A = inputs.gaussian(256, 2020)
+    H, Q = householder.hessenberg_reduce(A)
+    S, Z, wr, wi, info = api.schur(_dev(H), _dev(Q), n_shifts=8, aed_window=32)
+    assert info == 0
+    Sg, Zg = _np(S), _np(Z)
+    _check_result(A, Sg, Zg)
+    So, Zo, wro, wio, _ = qr.schur(H, Q, qr.Params(ns=8, nw=32))
+    _eig_match(_np(wr) + 1j * _np(wi), wro + 1j * wio, So, np.linalg.norm(H))
+
+
+@pytest.mark.parametrize("n", [8, 33, 100])
+def test_cyclic_and_companion(n):
+    """Matrices whose standard shifts stall (n-cycle) and a companion matrix
+    with known roots."""
+    H = testmats.cyclic(n)
+    S, Z, wr, wi, info = api.schur(_dev(H))
+    assert info == 0
+    lam = _np(wr) + 1j * _np(wi)
+    perm, dist = metrics.match_eigenvalues(lam, np.exp(2j * np.pi * np.arange(n) / n))
+    assert np.max(dist) < 1e-12
+    _check_result(H, _np(S), _np(Z))
+    roots = np.concatenate([np.arange(1, 6), -np.arange(1, 6), [2 + 1j, 2 - 1j]])
+    C = testmats.companion(roots)
+    S, Z, wr, wi, info = api.schur(_dev(C))
+    perm, dist = metrics.match_eigenvalues(_np(wr) + 1j * _np(wi), roots)
+    assert np.max(dist) < 1e-8
+
+
+def test_edge_cases():
+    """Decoupled blocks, a triangular input, padding (ld > n), accumulation
+    into a given Z, and non-finite input."""
+    n = 90
+    H = inputs.hessrand(n, 77)
+    H[30, 29] = 0.0
+    H[61, 60] = 0.0
+    S, Z, wr, wi, info = api.schur(_dev(H))
+    assert info == 0
+    _check_result(H, _np(S), _np(Z))
+    T = np.triu(inputs.hessrand(40, 5))
+    S, Z, wr, wi, info = api.schur(_dev(T))
+    assert np.allclose(np.sort(_np(wr)), np.sort(np.diag(T)), atol=1e-13)
+    big = torch.zeros((n + 7, n), dtype=torch.float64, device="cuda")
+    big[:n, :] = torch.from_numpy(H).cuda()
+    Hp = big.t().contiguous().t()[:n, :]   # strides (1, n+7)
+    assert Hp.stride() == (1, n + 7)
+    S, Z, wr, wi, info = api.schur(Hp)
+    _check_result(H, _np(S), _np(Z))
+    Q = testmats.haar_orthogonal(n, np.random.default_rng(1))
+    S, Z, wr, wi, info = api.schur(_dev(H), _dev(Q))
+    _check_result(Q @ H @ Q.T, _np(S), _np(Z))
+    Hn = H.copy()
+    Hn[5, 7] = np.nan
+    S, Z, wr, wi, info = api.schur(_dev(Hn), check=False)
+    assert info == -1001
+
+
+@pytest.mark.parametrize("mode", ["norm", "fixed"])
+def test_other_deflation_modes(mode):
+    H = inputs.hessrand(200, 9)
+    th = 1e-14 * np.linalg.norm(H)
+    S, Z, wr, wi, info = api.schur(_dev(H), deflation=mode, fixed_thold=th)
+    assert info == 0
+    _check_result(H, _np(S), _np(Z))
+    So, Zo, wro, wio, _ = qr.schur(H, params=qr.Params(deflation=mode, thold=th))
+    _eig_match(_np(wr) + 1j * _np(wi), wro + 1j * wio, So, np.linalg.norm(H))
+
+
+def test_big_aed_window_recursion():
+    """AED window larger than one thread block holds (nw = 200 > 160): the
+    window is reduced by the recursive multishift iteration."""
+    n = 700
+    H = inputs.hessrand(n, 11)
+    S, Z, wr, wi, info = api.schur(_dev(H), n_shifts=32, aed_window=200)
+    assert info == 0
+    _check_result(H, _np(S), _np(Z))
+    lam = _np(wr) + 1j * _np(wi)
+    nh = np.linalg.norm(H)
+    assert abs(np.sum(lam) - np.trace(H)) < 1e-12 * n * nh

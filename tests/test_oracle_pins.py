@@ -160,7 +160,7 @@ def test_cyclic_roots_of_unity(n):
     """P3: the n-cycle permutation (eigenvalues exp(2 pi i k / n)); standard
     shifts stall on it, so this exercises the exceptional shifts."""
     H = testmats.cyclic(n)
-    P = qr.Params(nmin=12) if n >= 31 else qr.Params()
+    P = qr.Params(nmin=12, nwin_francis=12) if n >= 31 else qr.Params()
     S, Z, wr, wi, info = qr.schur(H, params=P)
     assert info == 0
     _eig_close(wr + 1j * wi, np.exp(2j * np.pi * np.arange(n) / n), 1e-12)
@@ -378,7 +378,7 @@ def test_aed_recursive_window():
     algorithm")."""
     n = 120
     H = inputs.hessrand(n, 77)
-    S, Z, wr, wi, info = qr.schur(H, params=qr.Params(nmin=12, ns=6, nw=40))
+    S, Z, wr, wi, info = qr.schur(H, params=qr.Params(nmin=12, nwin_francis=12, ns=6, nw=40))
     assert info == 0
     _check_schur(H, S, Z)
     _eig_close(wr + 1j * wi, scipy.linalg.eigvals(H), 1e-9 * np.linalg.norm(H))
