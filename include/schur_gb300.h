@@ -73,6 +73,8 @@ typedef struct {
   void* stream;        /* cudaStream_t */
   void* workspace;     /* optional device scratch (see conventions) */
   size_t workspace_bytes;
+  int timing;          /* 1: record per-phase device time (CUDA events) in
+                          schur_stats; 0 (default): no events */
 } schur_opts;
 
 /* Statistics of the last schur_hessenberg call on this host thread. */
@@ -85,6 +87,20 @@ typedef struct {
   double sweep_gemm_flops;  /* executed FP64 flops of the off-window updates */
   double aed_gemm_flops;
   double reflector_flops;   /* algorithmic flops of direct reflector application */
+  int update_launches;      /* off-window product launches of the sweeps */
+  int chase_launches;       /* bulge-chase launches at the top level */
+  /* device time per phase in ms (opts->timing = 1 only): */
+  double t_chase_ms;        /* bulge-chase windows of the sweeps */
+  double t_update_ms;       /* off-window products of the sweeps */
+  double t_aed_ms;          /* AED: window Schur form, deflation, reordering */
+  double t_aed_update_ms;   /* off-window products of AED */
+  double t_small_ms;        /* double-shift QR of small blocks (+ products) */
+  /* SM clock cycles spent by the top-level AED kernels in the window Schur
+   * form (Sec. 2.5 step 1; windows held in shared memory only) and in the
+   * deflation checks + reordering + spike elimination (steps 2-3): */
+  double aed_cycles_schur;
+  double aed_cycles_post;
+  long long kernel_launches; /* kernels launched by the call (all levels) */
 } schur_stats;
 
 /* Fill *opts with the defaults listed above. Returns SCHUR_OK. */
@@ -118,6 +134,10 @@ int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, double* wr, 
 
 /* Statistics of the last schur_hessenberg call made by this host thread. */
 int schur_last_stats(schur_stats* out);
+
+/* Text of the last CUDA error seen by this host thread (which runtime call
+ * failed and where); "" if none.  Static storage, per host thread. */
+const char* schur_last_error_detail(void);
 
 /*
  * schur_hessenberg_batched -- the same reduction for `batch` independent
@@ -214,6 +234,15 @@ int schur_small_qr(int n, double* H, int ldh, double* Z, int ldz, int ilo, int i
  */
 int schur_apply_u(int side, double* A, int lda, int r0, int c0, int m, int k, const double* U, int ldu,
                   const schur_opts* opts);
+
+/*
+ * schur_fastmath_eval -- diagnostic of the FP64 reciprocal and reciprocal
+ * square root used on the latency-bound scalar paths (Newton-Raphson from an
+ * FP32 seed; not in the paper).  For each x[i] (device, length n) writes
+ * out[4i..4i+3] (device) = {fast 1/x, IEEE 1/x, fast 1/sqrt(x), IEEE
+ * 1/sqrt(x)} (the square-root pair is 0 for x <= 0).
+ */
+int schur_fastmath_eval(int n, const double* x, double* out, const schur_opts* opts);
 
 #ifdef __cplusplus
 }

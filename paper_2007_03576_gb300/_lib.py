@@ -43,6 +43,7 @@ class SchurOpts(ctypes.Structure):
         ("stream", c_void_p),
         ("workspace", c_void_p),
         ("workspace_bytes", c_size_t),
+        ("timing", c_int),
     ]
 
 
@@ -56,6 +57,16 @@ class SchurStats(ctypes.Structure):
         ("sweep_gemm_flops", c_double),
         ("aed_gemm_flops", c_double),
         ("reflector_flops", c_double),
+        ("update_launches", c_int),
+        ("chase_launches", c_int),
+        ("t_chase_ms", c_double),
+        ("t_update_ms", c_double),
+        ("t_aed_ms", c_double),
+        ("t_aed_update_ms", c_double),
+        ("t_small_ms", c_double),
+        ("aed_cycles_schur", c_double),
+        ("aed_cycles_post", c_double),
+        ("kernel_launches", ctypes.c_longlong),
     ]
 
 
@@ -65,6 +76,7 @@ _SIGS = {
     "schur_workspace_size": (c_int, [c_int, P(SchurOpts), P(c_size_t)]),
     "schur_hessenberg": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, P(SchurOpts)]),
     "schur_last_stats": (c_int, [P(SchurStats)]),
+    "schur_last_error_detail": (ctypes.c_char_p, []),
     "schur_hessenberg_batched": (c_int, [c_int, P(c_int), P(c_void_p), P(c_int), P(c_void_p), P(c_int),
                                          P(c_void_p), P(c_void_p), P(c_int), P(SchurOpts)]),
     "schur_eig_backward": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
@@ -79,6 +91,7 @@ _SIGS = {
     "schur_small_qr": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_int, c_int, P(SchurOpts)]),
     "schur_apply_u": (c_int, [c_int, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_int,
                               P(SchurOpts)]),
+    "schur_fastmath_eval": (c_int, [c_int, c_void_p, c_void_p, P(SchurOpts)]),
 }
 
 _LIB = None
@@ -123,4 +136,7 @@ def make_opts(stream=0, **kw):
 
 
 def status(code):
-    return load().schur_status_string(int(code)).decode()
+    s = load().schur_status_string(int(code)).decode()
+    if int(code) == SCHUR_ERR_CUDA:
+        s += ": " + load().schur_last_error_detail().decode()
+    return s

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fastmath.cuh"
+
 #define SCHUR_U (2.220446049250313080847e-16)     /* u = 2^-52, Sec. 5.4 */
 #define SCHUR_NU (2.225073858507201383090e-308)   /* nu = DBL_MIN, Sec. 5.6 */
 
@@ -36,7 +38,8 @@ struct Ctl {
   int ndfl;      // iterations since the last deflation (exceptional shifts)
   int info;      // nonzero: small-QR / window-QR iteration limit
   int swap_fail; // a reordering swap was rejected in the last AED
-  int pad;
+  int nswaps;    // swaps performed by the last AED
+  long long cyc_schur, cyc_defl, cyc_hess;  // clock64 cycles of the AED sub-steps (accumulated)
 };
 
 // One bulge chain in one launch of the chase kernel (Sec. 2.3 / 2.4: a set of
@@ -91,18 +94,34 @@ struct Mat {
 __device__ __forceinline__ double smlnum_of(int n) { return SCHUR_NU * ((double)n / SCHUR_U); }
 
 // Householder reflector (I - tau v v^T), v = (1, v1, v2) (v2 = 0 when nr == 2),
-// with (I - tau v v^T) x = beta e_1, beta = -sign(x0) ||x||.
+// with (I - tau v v^T) x = beta e_1, beta = -sign(x0) ||x||.  With
+// r = 1/||x|| and d = x0 - beta: v = x / d, tau = -d / beta = sign(x0) d r,
+// so one reciprocal square root and one reciprocal suffice (fastmath.cuh);
+// operands whose squares could overflow/underflow take the hypot path.
 __device__ __forceinline__ void house3(int nr, double x0, double x1, double x2, double& v1, double& v2,
                                        double& tau, double& beta) {
   if (nr < 3) x2 = 0.0;
-  double sig = (nr >= 3) ? hypot(x1, x2) : fabs(x1);
-  if (nr < 2 || sig == 0.0) {
+  if (nr < 2 || (fm_abs_key(x1) | fm_abs_key(x2)) == 0) {
     v1 = 0.0;
     v2 = 0.0;
     tau = 0.0;
     beta = x0;
     return;
   }
+  const bool neg = __double2hiint(x0) < 0;
+  if (fm_safe_range3(x0, x1, x2)) {
+    double a = fma(x0, x0, fma(x1, x1, x2 * x2));
+    double r = fast_rsqrt(a);
+    double nrm = a * r;
+    beta = neg ? nrm : -nrm;
+    double d = x0 - beta;
+    double rd = fast_rcp(d);
+    v1 = x1 * rd;
+    v2 = x2 * rd;
+    tau = neg ? -d * r : d * r;
+    return;
+  }
+  double sig = hypot(x1, x2);
   double nrm = hypot(x0, sig);
   beta = -copysign(nrm, x0);
   tau = (beta - x0) / beta;
@@ -133,11 +152,13 @@ __device__ __forceinline__ void eig2x2(double a, double b, double c, double d, d
 // Rotation G = [[cs, -sn], [sn, cs]] with G^T A G in standard form
 // (eq. 2by2_blocks): complex pair -> equal diagonal, b'c' < 0; real
 // eigenvalues -> c' = 0.  Real case: G e_1 is a unit eigenvector of the
-// eigenvalue (a+d)/2 + sign(a-d) r; complex case: the angle
-// t = atan2(-(a-d), b+c)/2 zeroes the diagonal difference
-// (a-d) cos 2t + (b+c) sin 2t.  Writes the new block to B[4] = a', b', c', d'.
+// eigenvalue (a+d)/2 + sign(a-d) r.  Complex case: the diagonal difference
+// of G^T A G is (a-d) cos 2t + (b+c) sin 2t, zero for
+// (cos 2t, sin 2t) = (|b+c|, -sign(b+c) (a-d)) / rho, rho = ||(a-d, b+c)||
+// (the root with cos 2t >= 0), and cos t = sqrt((1 + cos 2t)/2),
+// sin t = sin 2t / (2 cos t).  Writes the new block to B[4] = a', b', c', d'.
 __device__ inline void standardize2x2(double a, double b, double c, double d, double& cs, double& sn, double* B) {
-  if (c == 0.0) {
+  if (fm_abs_key(c) == 0) {
     cs = 1.0;
     sn = 0.0;
     B[0] = a; B[1] = b; B[2] = 0.0; B[3] = d;
@@ -145,21 +166,40 @@ __device__ inline void standardize2x2(double a, double b, double c, double d, do
   }
   for (int pass = 0; pass < 2; ++pass) {
     double p = 0.5 * (a - d);
-    double disc = p * p + b * c;
-    double c1, s1;
-    if (disc >= 0.0) {
-      double r = sqrt(disc);
+    double disc = fma(p, p, b * c);
+    bool real = __double2hiint(disc) >= 0;
+    double c1 = 1.0, s1 = 0.0;
+    if (real) {
+      double r = (fm_abs_key(disc) == 0) ? 0.0 : disc * fast_rsqrt(disc);
       double z = p + copysign(r, p);
       double lam1 = d + z;
       double u0 = z, u1 = c, w0 = b, w1 = lam1 - a;
       if (fabs(u0) + fabs(u1) < fabs(w0) + fabs(w1)) { u0 = w0; u1 = w1; }
-      double nrm = hypot(u0, u1);
-      c1 = u0 / nrm;
-      s1 = u1 / nrm;
+      if (fm_safe_range3(u0, u1, 0.0)) {
+        double rn = fast_rsqrt(fma(u0, u0, u1 * u1));
+        c1 = u0 * rn;
+        s1 = u1 * rn;
+      } else {
+        double nrm = hypot(u0, u1);
+        c1 = u0 / nrm;
+        s1 = u1 / nrm;
+      }
     } else {
-      double t = 0.5 * atan2(-(a - d), b + c);
-      c1 = cos(t);
-      s1 = sin(t);
+      double am = a - d, bp = b + c;
+      double rho2 = fma(am, am, bp * bp);
+      if (fm_abs_key(rho2) != 0 && fm_safe_range3(am, bp, 0.0)) {
+        double rr = fast_rsqrt(rho2);
+        double c2 = fabs(bp) * rr;
+        double s2 = (__double2hiint(bp) < 0 ? am : -am) * rr;
+        double h = 0.5 * (1.0 + c2);
+        double rs = fast_rsqrt(h);
+        c1 = h * rs;
+        s1 = 0.5 * s2 * rs;
+      } else if (fm_abs_key(rho2) != 0) {
+        double t = 0.5 * atan2(-(a - d), b + c);
+        c1 = cos(t);
+        s1 = sin(t);
+      }
     }
     // B = G^T A G
     double t00 = a * c1 + b * s1, t01 = -a * s1 + b * c1;
@@ -174,7 +214,7 @@ __device__ inline void standardize2x2(double a, double b, double c, double d, do
       cs = cc;
       sn = ss;
     }
-    if (disc >= 0.0) {
+    if (real) {
       B[0] = na; B[1] = nb; B[2] = 0.0; B[3] = nd;
       return;
     }
@@ -185,7 +225,7 @@ __device__ inline void standardize2x2(double a, double b, double c, double d, do
     }
     // rounding made the pair real: triangularise the rotated block
     a = m; b = nb; c = nc; d = m;
-    if (c == 0.0) {
+    if (fm_abs_key(c) == 0) {
       B[0] = a; B[1] = b; B[2] = 0.0; B[3] = d;
       return;
     }
@@ -212,8 +252,8 @@ __device__ inline bool subdiag_negligible(const Mat& H, int k, int lo, int hi, c
   double h22 = fabs(H(k, k));
   double ab = fmax(h21, h12), ba = fmin(h21, h12);
   double aa = fmax(h22, dd), bb = fmin(h22, dd);
-  double s = aa + ab;
-  return ba * (ab / s) <= fmax(sml, SCHUR_U * (bb * (aa / s)));
+  double rs = fast_rcp(aa + ab);
+  return ba * (ab * rs) <= fmax(sml, SCHUR_U * (bb * (aa * rs)));
 }
 
 // AED deflation test (Sec. 5.6) of the block of T ending at row j (size bs)

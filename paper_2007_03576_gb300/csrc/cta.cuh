@@ -14,6 +14,7 @@
 struct CtaShared {
   double r[8];       // reflector / rotation broadcast
   double q[16];      // 4x4 orthogonal factor of a swap
+  double d[16];      // new 4x4 diagonal block of a swap
   double red[32];    // block reductions
   int iv[8];         // integer broadcast
 };
@@ -129,6 +130,10 @@ __device__ inline void cta_standardize_block(const Mat& T, int k, int ncols, con
 // ---------------------------------------------------------------------------
 // One Francis double-shift sweep on [l, i] of the m x m matrix T (full Schur
 // mode within T: columns up to m-1, rows from 0), accumulated into U.
+// Per reflector: thread 0 builds it (a short FP64 chain, see house3), then
+// the left product on rows k..k+2 and the right product on columns k..k+2
+// (and U) run over all threads, separated by a barrier because they meet on
+// the 3x3 diagonal block.
 // ---------------------------------------------------------------------------
 __device__ inline void cta_double_shift_sweep(const Mat& T, int m, int l, int i, double ssum, double sprod,
                                               const Mat& U, int urows, CtaShared* sh) {
@@ -138,7 +143,7 @@ __device__ inline void cta_double_shift_sweep(const Mat& T, int m, int l, int i,
       double x0, x1, x2 = 0.0;
       if (k == l) {
         double h00 = T(l, l), h01 = T(l, l + 1), h10 = T(l + 1, l), h11 = T(l + 1, l + 1);
-        x0 = h00 * h00 + h01 * h10 - ssum * h00 + sprod;
+        x0 = fma(h00, h00, fma(h01, h10, fma(-ssum, h00, sprod)));
         x1 = h10 * (h00 + h11 - ssum);
         if (nr == 3) x2 = h10 * T(l + 2, l + 1);
       } else {
@@ -159,10 +164,29 @@ __device__ inline void cta_double_shift_sweep(const Mat& T, int m, int l, int i,
     }
     __syncthreads();
     double v1 = sh->r[0], v2 = sh->r[1], tau = sh->r[2];
-    cta_refl_left(T, k, nr, v1, v2, tau, k, m - 1);
-    __syncthreads();
-    cta_refl_right(T, k, nr, v1, v2, tau, 0, min(k + 3, i));
-    if (U.p) cta_refl_right(U, k, nr, v1, v2, tau, 0, urows - 1);
+    if (tau != 0.0) {
+      for (int j = k + cta_tid(); j < m; j += cta_nt()) {
+        double* col = &T(k, j);
+        double a0 = col[0], a1 = col[1], a2 = (nr == 3) ? col[2] : 0.0;
+        double s = tau * fma(v2, a2, fma(v1, a1, a0));
+        col[0] = a0 - s;
+        col[1] = fma(-s, v1, a1);
+        if (nr == 3) col[2] = fma(-s, v2, a2);
+      }
+      __syncthreads();
+      const int nrr = min(k + 3, i) + 1;   // rows 0..min(k+3, i) of T
+      const int nu = U.p ? urows : 0;
+      for (int it = cta_tid(); it < nrr + nu; it += cta_nt()) {
+        const Mat& M = (it < nrr) ? T : U;
+        int r = (it < nrr) ? it : it - nrr;
+        double* c0 = &M(r, k);
+        double a0 = c0[0], a1 = c0[M.ld], a2 = (nr == 3) ? c0[2 * M.ld] : 0.0;
+        double s = tau * fma(v2, a2, fma(v1, a1, a0));
+        c0[0] = a0 - s;
+        c0[M.ld] = fma(-s, v1, a1);
+        if (nr == 3) c0[2 * M.ld] = fma(-s, v2, a2);
+      }
+    }
     __syncthreads();
   }
 }
@@ -221,193 +245,262 @@ __device__ inline int cta_francis(const Mat& T, int m, int lo, int hi, const Mat
 // Sec. 2.5): T[j:j+p] (p x p) and the following q x q block.
 // ---------------------------------------------------------------------------
 
+// Householder vector of x (length len <= 4): (I - tau v v^T) x = beta e_1.
+__device__ inline void house_small(int len, const double* x, double* v, double& tau, double& beta) {
+  v[0] = 1.0;
+  long long rest = 0;
+  for (int t = 1; t < len; ++t) rest |= fm_abs_key(x[t]);
+  if (rest == 0) {
+    for (int t = 1; t < len; ++t) v[t] = 0.0;
+    tau = 0.0;
+    beta = x[0];
+    return;
+  }
+  bool safe = true;
+  for (int t = 0; t < len; ++t) {
+    int e = fm_exponent(x[t]);
+    if (fm_abs_key(x[t]) != 0 && (e <= -480 || e >= 480)) safe = false;
+  }
+  const bool neg = __double2hiint(x[0]) < 0;
+  if (safe) {
+    double a = 0.0;
+    for (int t = 0; t < len; ++t) a = fma(x[t], x[t], a);
+    double r = fast_rsqrt(a);
+    double nrm = a * r;
+    beta = neg ? nrm : -nrm;
+    double d = x[0] - beta;
+    double rd = fast_rcp(d);
+    for (int t = 1; t < len; ++t) v[t] = x[t] * rd;
+    tau = neg ? -d * r : d * r;
+    return;
+  }
+  double sig = 0.0;
+  for (int t = 1; t < len; ++t) sig = hypot(sig, x[t]);
+  double nrm = hypot(x[0], sig);
+  beta = neg ? nrm : -nrm;
+  double d = x[0] - beta;
+  for (int t = 1; t < len; ++t) v[t] = x[t] / d;
+  tau = (beta - x[0]) / beta;
+}
+
 // Householder QR of the m x q matrix W (m <= 4, q <= 2); returns the m x m
-// orthogonal factor in Q (column-major).
-__device__ inline void small_qr_q(double W[4][2], int m, int q, double Q[16]) {
+// orthogonal factor in Q (column-major, leading dimension 4).
+__device__ inline void small_qr_q(double W[4][2], int m, int q, double* Q) {
   for (int a = 0; a < m; ++a)
     for (int b = 0; b < m; ++b) Q[a + 4 * b] = (a == b) ? 1.0 : 0.0;
   for (int c = 0; c < q; ++c) {
     int len = m - c;
-    double scale = 0.0;
-    for (int t = 0; t < len; ++t) scale = fmax(scale, fabs(W[c + t][c]));
-    if (scale == 0.0) continue;
-    double ss = 0.0;
-    for (int t = 1; t < len; ++t) {
-      double z = W[c + t][c] / scale;
-      ss += z * z;
-    }
-    if (ss == 0.0) continue;
-    double alpha = W[c][c];
-    double sig = scale * sqrt(ss);
-    double beta = -copysign(hypot(alpha, sig), alpha);
-    double tau = (beta - alpha) / beta;
-    double v[4];
-    v[0] = 1.0;
-    for (int t = 1; t < len; ++t) v[t] = W[c + t][c] / (alpha - beta);
+    double x[4], v[4], tau, beta;
+    for (int t = 0; t < len; ++t) x[t] = W[c + t][c];
+    house_small(len, x, v, tau, beta);
+    if (tau == 0.0) continue;
     for (int cc = c; cc < q; ++cc) {
       double s = 0.0;
-      for (int t = 0; t < len; ++t) s += v[t] * W[c + t][cc];
+      for (int t = 0; t < len; ++t) s = fma(v[t], W[c + t][cc], s);
       s *= tau;
-      for (int t = 0; t < len; ++t) W[c + t][cc] -= s * v[t];
+      for (int t = 0; t < len; ++t) W[c + t][cc] = fma(-s, v[t], W[c + t][cc]);
     }
     for (int r = 0; r < m; ++r) {
       double s = 0.0;
-      for (int t = 0; t < len; ++t) s += Q[r + 4 * (c + t)] * v[t];
+      for (int t = 0; t < len; ++t) s = fma(Q[r + 4 * (c + t)], v[t], s);
       s *= tau;
-      for (int t = 0; t < len; ++t) Q[r + 4 * (c + t)] -= s * v[t];
+      for (int t = 0; t < len; ++t) Q[r + 4 * (c + t)] = fma(-s, v[t], Q[r + 4 * (c + t)]);
     }
   }
 }
 
-// Thread-0 part of the swap: builds Q (returned in sh->q) and tests the
-// result.  Returns true if the swap is accepted.
-__device__ inline bool swap_compute(const Mat& T, int nT, int j, int p, int q, CtaShared* sh) {
-  int m = p + q;
-  double A[4][4];
-  double fro = 0.0;
-  for (int a = 0; a < m; ++a)
-    for (int b = 0; b < m; ++b) {
-      A[a][b] = T(j + a, j + b);
-      fro += A[a][b] * A[a][b];
-    }
-  fro = sqrt(fro);
-  // Sylvester A11 X - X A22 = A12 as a (pq x pq) Kronecker system, vec(X)
-  // column-major: index r + c*p.
-  int pq = p * q;
-  double K[4][4], rhs[4];
-  double kmax = 0.0;
-  for (int c = 0; c < q; ++c)
-    for (int r = 0; r < p; ++r) {
-      int row = r + c * p;
-      rhs[row] = A[r][p + c];
-      for (int c2 = 0; c2 < q; ++c2)
-        for (int r2 = 0; r2 < p; ++r2) {
-          int col = r2 + c2 * p;
-          double v = ((c == c2) ? A[r][r2] : 0.0) - ((r == r2) ? A[p + c2][p + c] : 0.0);
-          K[row][col] = v;
-          kmax = fmax(kmax, fabs(v));
+// Warp 0 part of the swap (all 32 lanes call it).  Lane 0 solves the
+// Sylvester equation A11 X - X A22 = A12 (its Kronecker form, complete
+// pivoting by magnitude keys, a pivot below sml replaced by sml as Bai &
+// Demmel do for nearly equal eigenvalues) and factors [-X; I] = Q [R; 0];
+// lanes (a, b) then form D = Q^T A Q in parallel, D's (2,1) block is the
+// residual of the swap (accepted if <= max(10 u ||A||_F, nu n / u)) and is
+// set to zero.  Two 1x1 blocks [[a, b], [0, c]] swap by the rotation whose
+// first column is (b, c - a)/norm, which the Sylvester solution
+// x = b / (a - c) gives; its residual is zero by construction.
+// Results: sh->q (Q), sh->d (D), sh->iv[1] (1 = accepted).
+__device__ inline void warp_swap_compute(const Mat& T, int nT, int j, int p, int q, CtaShared* sh) {
+  const int lane = threadIdx.x & 31;
+  const int m = p + q;
+  double* Q = sh->q;
+  double* D = sh->d;
+  if (p == 1 && q == 1) {
+    if (lane == 0) {
+      double a = T(j, j), b = T(j, j + 1), c = T(j + 1, j + 1);
+      double u0 = b, u1 = c - a;
+      double cs = 1.0, sn = 0.0;
+      if ((fm_abs_key(u0) | fm_abs_key(u1)) != 0) {
+        if (fm_safe_range3(u0, u1, 0.0)) {
+          double r = fast_rsqrt(fma(u0, u0, u1 * u1));
+          cs = u0 * r;
+          sn = u1 * r;
+        } else {
+          double r = hypot(u0, u1);
+          cs = u0 / r;
+          sn = u1 / r;
         }
+      }
+      double t00 = fma(a, cs, b * sn), t01 = fma(-a, sn, b * cs);
+      double t10 = c * sn, t11 = c * cs;
+      D[0] = fma(cs, t00, sn * t10);
+      D[1] = 0.0;
+      D[4] = fma(cs, t01, sn * t11);
+      D[5] = fma(-sn, t01, cs * t11);
+      Q[0] = cs; Q[1] = sn; Q[4] = -sn; Q[5] = cs;
+      sh->iv[1] = 1;
     }
-  double sml = fmax(SCHUR_U * kmax, smlnum_of(nT));
-  int perm[4] = {0, 1, 2, 3};
-  for (int i = 0; i < pq; ++i) {
-    int br = i, bc = i;
-    double best = -1.0;
-    for (int r = i; r < pq; ++r)
-      for (int c = i; c < pq; ++c)
-        if (fabs(K[r][c]) > best) {
-          best = fabs(K[r][c]);
-          br = r;
-          bc = c;
+    return;
+  }
+  if (lane == 0) {
+    int pq = p * q;
+    double K[4][4], rhs[4];
+    long long kmax = 0;
+    for (int c = 0; c < q; ++c)
+      for (int r = 0; r < p; ++r) {
+        int row = r + c * p;
+        rhs[row] = T(j + r, j + p + c);
+        for (int c2 = 0; c2 < q; ++c2)
+          for (int r2 = 0; r2 < p; ++r2) {
+            int col = r2 + c2 * p;
+            double v = ((c == c2) ? T(j + r, j + r2) : 0.0) - ((r == r2) ? T(j + p + c2, j + p + c) : 0.0);
+            K[row][col] = v;
+            long long kk = fm_abs_key(v);
+            kmax = kk > kmax ? kk : kmax;
+          }
+      }
+    double sml = fmax(SCHUR_U * __longlong_as_double(kmax), smlnum_of(nT));
+    long long smlk = fm_abs_key(sml);
+    int perm[4] = {0, 1, 2, 3};
+    double inv[4];
+    for (int i = 0; i < pq; ++i) {
+      int br = i, bc = i;
+      long long best = -1;
+      for (int r = i; r < pq; ++r)
+        for (int c = i; c < pq; ++c) {
+          long long kk = fm_abs_key(K[r][c]);
+          if (kk > best) {
+            best = kk;
+            br = r;
+            bc = c;
+          }
         }
-    if (br != i) {
-      for (int c = 0; c < pq; ++c) {
-        double t = K[i][c]; K[i][c] = K[br][c]; K[br][c] = t;
+      if (br != i) {
+        for (int c = 0; c < pq; ++c) {
+          double t = K[i][c]; K[i][c] = K[br][c]; K[br][c] = t;
+        }
+        double t = rhs[i]; rhs[i] = rhs[br]; rhs[br] = t;
       }
-      double t = rhs[i]; rhs[i] = rhs[br]; rhs[br] = t;
-    }
-    if (bc != i) {
-      for (int r = 0; r < pq; ++r) {
-        double t = K[r][i]; K[r][i] = K[r][bc]; K[r][bc] = t;
+      if (bc != i) {
+        for (int r = 0; r < pq; ++r) {
+          double t = K[r][i]; K[r][i] = K[r][bc]; K[r][bc] = t;
+        }
+        int t = perm[i]; perm[i] = perm[bc]; perm[bc] = t;
       }
-      int t = perm[i]; perm[i] = perm[bc]; perm[bc] = t;
+      if (best < smlk) K[i][i] = sml;
+      inv[i] = fast_rcp(K[i][i]);
+      for (int r = i + 1; r < pq; ++r) {
+        double f = K[r][i] * inv[i];
+        for (int c = i + 1; c < pq; ++c) K[r][c] = fma(-f, K[i][c], K[r][c]);
+        rhs[r] = fma(-f, rhs[i], rhs[r]);
+      }
     }
-    if (fabs(K[i][i]) < sml) K[i][i] = sml;
-    for (int r = i + 1; r < pq; ++r) {
-      double f = K[r][i] / K[i][i];
-      for (int c = i; c < pq; ++c) K[r][c] -= f * K[i][c];
-      rhs[r] -= f * rhs[i];
+    double y[4], x[4];
+    for (int i = pq - 1; i >= 0; --i) {
+      double s = rhs[i];
+      for (int c = i + 1; c < pq; ++c) s = fma(-K[i][c], y[c], s);
+      y[i] = s * inv[i];
     }
+    for (int i = 0; i < pq; ++i) x[perm[i]] = y[i];
+    double W[4][2];
+    for (int r = 0; r < m; ++r)
+      for (int c = 0; c < 2; ++c) W[r][c] = 0.0;
+    for (int c = 0; c < q; ++c) {
+      for (int r = 0; r < p; ++r) W[r][c] = -x[r + c * p];
+      W[p + c][c] = 1.0;
+    }
+    small_qr_q(W, m, q, Q);
   }
-  double y[4], x[4];
-  for (int i = pq - 1; i >= 0; --i) {
-    double s = rhs[i];
-    for (int c = i + 1; c < pq; ++c) s -= K[i][c] * y[c];
-    y[i] = s / K[i][i];
-  }
-  for (int i = 0; i < pq; ++i) x[perm[i]] = y[i];
-  // W = [-X; I] (m x q)
-  double W[4][2];
-  for (int r = 0; r < m; ++r)
-    for (int c = 0; c < 2; ++c) W[r][c] = 0.0;
-  for (int c = 0; c < q; ++c) {
-    for (int r = 0; r < p; ++r) W[r][c] = -x[r + c * p];
-    W[p + c][c] = 1.0;
-  }
-  double Q[16];
-  small_qr_q(W, m, q, Q);
-  // residual: (Q^T A Q)[q:m, 0:q]
-  double AQ[4][4];
-  for (int a = 0; a < m; ++a)
-    for (int b = 0; b < m; ++b) {
-      double s = 0.0;
-      for (int t = 0; t < m; ++t) s += A[a][t] * Q[t + 4 * b];
-      AQ[a][b] = s;
+  __syncwarp();
+  // D = Q^T A Q, one entry per lane
+  const int a = lane & 3, b = lane >> 2;
+  const bool mine = lane < 16 && a < m && b < m;
+  double dab = 0.0, fro = 0.0;
+  if (mine) {
+    for (int t = 0; t < m; ++t) {
+      double aq = 0.0;
+      for (int s2 = 0; s2 < m; ++s2) aq = fma(T(j + t, j + s2), Q[s2 + 4 * b], aq);
+      dab = fma(Q[t + 4 * a], aq, dab);
     }
-  double res = 0.0;
-  for (int a = q; a < m; ++a)
-    for (int b = 0; b < q; ++b) {
-      double s = 0.0;
-      for (int t = 0; t < m; ++t) s += Q[t + 4 * a] * AQ[t][b];
-      res += s * s;
-    }
-  res = sqrt(res);
-  for (int t = 0; t < 16; ++t) sh->q[t] = Q[t];
-  return res <= fmax(10.0 * SCHUR_U * fro, smlnum_of(nT));
+    double av = T(j + a, j + b);
+    fro = av * av;
+  }
+  double res = (mine && a >= q && b < q) ? dab * dab : 0.0;
+  for (int o = 16; o > 0; o >>= 1) {
+    res += __shfl_xor_sync(0xffffffffu, res, o);
+    fro += __shfl_xor_sync(0xffffffffu, fro, o);
+  }
+  if (mine) D[a + 4 * b] = (a >= q && b < q) ? 0.0 : dab;
+  if (lane == 0) {
+    double tol = 10.0 * SCHUR_U;
+    double sml = smlnum_of(nT);
+    sh->iv[1] = (res <= fmax(tol * tol * fro, sml * sml)) ? 1 : 0;
+  }
 }
 
 // Swap the adjacent blocks (sizes p, q) starting at row j of the nT x nT
 // quasi-triangular T, accumulating into V (vrows x nT).  Returns false (T, V
-// untouched) when the swap is rejected.
+// untouched) when the swap is rejected.  The swapped blocks are left as the
+// orthogonal factor produces them (not re-standardised: callers standardise
+// a block when its standard form is needed).  Two barriers: the diagonal
+// block is written from D while the other threads apply Q to the rest of the
+// rows (columns >= j+m), the rest of the columns (rows < j) and V.
 __device__ inline bool cta_swap(const Mat& T, int nT, int j, int p, int q, const Mat& V, int vrows, CtaShared* sh) {
-  if (cta_tid() == 0) sh->iv[1] = swap_compute(T, nT, j, p, q, sh) ? 1 : 0;
+  if (cta_tid() < 32) warp_swap_compute(T, nT, j, p, q, sh);
   __syncthreads();
-  bool ok = sh->iv[1] != 0;
-  if (!ok) {
+  if (sh->iv[1] == 0) {
     __syncthreads();
     return false;
   }
-  int m = p + q;
+  const int m = p + q;
   const double* Q = sh->q;
-  for (int c = j + cta_tid(); c < nT; c += cta_nt()) {  // rows j..j+m-1 <- Q^T rows
+  const int nrest_c = nT - (j + m);  // columns right of the block
+  const int nrest_r = j;             // rows above the block
+  const int total = nrest_c + nrest_r + vrows + 1;
+  for (int it = cta_tid(); it < total; it += cta_nt()) {
     double x[4], y[4];
-    for (int t = 0; t < m; ++t) x[t] = T(j + t, c);
-    for (int a = 0; a < m; ++a) {
-      double s = 0.0;
-      for (int t = 0; t < m; ++t) s += Q[t + 4 * a] * x[t];
-      y[a] = s;
+    if (it < nrest_c) {
+      int c = j + m + it;
+      for (int t = 0; t < m; ++t) x[t] = T(j + t, c);
+      for (int a = 0; a < m; ++a) {
+        double s = 0.0;
+        for (int t = 0; t < m; ++t) s += Q[t + 4 * a] * x[t];
+        y[a] = s;
+      }
+      for (int t = 0; t < m; ++t) T(j + t, c) = y[t];
+    } else if (it < nrest_c + nrest_r) {
+      int r = it - nrest_c;
+      for (int t = 0; t < m; ++t) x[t] = T(r, j + t);
+      for (int b = 0; b < m; ++b) {
+        double s = 0.0;
+        for (int t = 0; t < m; ++t) s += x[t] * Q[t + 4 * b];
+        y[b] = s;
+      }
+      for (int t = 0; t < m; ++t) T(r, j + t) = y[t];
+    } else if (it < nrest_c + nrest_r + vrows) {
+      int r = it - nrest_c - nrest_r;
+      for (int t = 0; t < m; ++t) x[t] = V(r, j + t);
+      for (int b = 0; b < m; ++b) {
+        double s = 0.0;
+        for (int t = 0; t < m; ++t) s += x[t] * Q[t + 4 * b];
+        y[b] = s;
+      }
+      for (int t = 0; t < m; ++t) V(r, j + t) = y[t];
+    } else {
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) T(j + a, j + b) = sh->d[a + 4 * b];
     }
-    for (int t = 0; t < m; ++t) T(j + t, c) = y[t];
   }
   __syncthreads();
-  for (int r = cta_tid(); r < j + m; r += cta_nt()) {  // columns j..j+m-1 <- cols Q
-    double x[4], y[4];
-    for (int t = 0; t < m; ++t) x[t] = T(r, j + t);
-    for (int b = 0; b < m; ++b) {
-      double s = 0.0;
-      for (int t = 0; t < m; ++t) s += x[t] * Q[t + 4 * b];
-      y[b] = s;
-    }
-    for (int t = 0; t < m; ++t) T(r, j + t) = y[t];
-  }
-  for (int r = cta_tid(); r < vrows; r += cta_nt()) {
-    double x[4], y[4];
-    for (int t = 0; t < m; ++t) x[t] = V(r, j + t);
-    for (int b = 0; b < m; ++b) {
-      double s = 0.0;
-      for (int t = 0; t < m; ++t) s += x[t] * Q[t + 4 * b];
-      y[b] = s;
-    }
-    for (int t = 0; t < m; ++t) V(r, j + t) = y[t];
-  }
-  __syncthreads();
-  if (cta_tid() == 0) {
-    for (int a = q; a < m; ++a)
-      for (int b = 0; b < q; ++b) T(j + a, j + b) = 0.0;
-  }
-  __syncthreads();
-  if (q == 2) cta_standardize_block(T, j, nT, V, vrows, sh);
-  if (p == 2) cta_standardize_block(T, j + q, nT, V, vrows, sh);
   return true;
 }
 
@@ -418,7 +511,6 @@ __device__ inline bool cta_move_block_up(const Mat& T, int nT, int ifst, int ils
   int here = ifst;
   while (here > ilst) {
     int q = (here >= 2 && here - 2 >= ilst && T(here - 1, here - 2) != 0.0) ? 2 : 1;
-    __syncthreads();
     if (!cta_swap(T, nT, here - q, q, p, V, vrows, sh)) return false;
     here -= q;
   }
@@ -445,11 +537,13 @@ __device__ inline void cta_house_vec(const double* x, int len, double* vbuf, dou
   __syncthreads();
   double scale = sh->r[6];
   double ss = 0.0;
-  if (scale > 0.0)
+  if (scale > 0.0) {
+    double rsc = fast_rcp(scale);
     for (int t = 1 + cta_tid(); t < len; t += cta_nt()) {
-      double z = x[t] / scale;
-      ss += z * z;
+      double z = x[t] * rsc;
+      ss = fma(z, z, ss);
     }
+  }
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
   __syncthreads();
   if ((cta_tid() & 31) == 0) sh->red[cta_tid() >> 5] = ss;
@@ -467,14 +561,14 @@ __device__ inline void cta_house_vec(const double* x, int len, double* vbuf, dou
       double b = -copysign(hypot(alpha, sig), alpha);
       sh->r[6] = (b - alpha) / b;
       sh->r[7] = b;
-      sh->r[5] = alpha - b;
+      sh->r[5] = 1.0 / (alpha - b);   // reciprocal of the scaling denominator
     }
   }
   __syncthreads();
   tau = sh->r[6];
   beta = sh->r[7];
-  double den = sh->r[5];
-  for (int t = cta_tid(); t < len; t += cta_nt()) vbuf[t] = (t == 0) ? 1.0 : ((tau == 0.0) ? 0.0 : x[t] / den);
+  double rden = sh->r[5];
+  for (int t = cta_tid(); t < len; t += cta_nt()) vbuf[t] = (t == 0) ? 1.0 : ((tau == 0.0) ? 0.0 : x[t] * rden);
   __syncthreads();
 }
 
@@ -513,11 +607,15 @@ __device__ inline void cta_house_right(const Mat& M, const double* v, int len, d
 // ---------------------------------------------------------------------------
 __device__ inline int cta_aed_post(const Mat& T, int nw, int info, double s, const Mat& V, const DeflParams& dp,
                                    double* vbuf, double* cand_re, double* cand_im, int* ncand_out, double* top_out,
-                                   int* swap_fail_out, CtaShared* sh) {
+                                   int* swap_fail_out, CtaShared* sh, long long* cyc = nullptr) {
+  long long c0 = clock64();
   int ns = nw;
   int ilst = info;
   int failed = 0;
   for (int guard = 0; guard < 2 * nw + 2 && ilst < ns; ++guard) {
+    // the bottom 2x2 block is put in standard form before it is tested
+    // (swaps leave moved blocks unstandardised)
+    if (ns >= 2 && T(ns - 1, ns - 2) != 0.0) cta_standardize_block(T, ns - 2, nw, V, nw, sh);
     // decision by thread 0
     if (cta_tid() == 0) {
       int bs = (ns >= 2 && T(ns - 1, ns - 2) != 0.0) ? 2 : 1;
@@ -542,6 +640,7 @@ __device__ inline int cta_aed_post(const Mat& T, int nw, int info, double s, con
     ilst += bs;
   }
   int nd = nw - ns;
+  long long c1 = clock64();
   // candidates of the undeflated part (converged rows info..ns-1)
   if (cta_tid() == 0) {
     int c = 0;
@@ -599,5 +698,9 @@ __device__ inline int cta_aed_post(const Mat& T, int nw, int info, double s, con
     }
   }
   *top_out = top;
+  if (cyc && cta_tid() == 0) {
+    cyc[0] += c1 - c0;
+    cyc[1] += clock64() - c1;
+  }
   return nd;
 }

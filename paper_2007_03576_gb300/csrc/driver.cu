@@ -135,8 +135,51 @@ void Solver::carve(char* base, int n) {
 static bool g_attr_done = false;
 static int g_num_sms = 0;
 
-static void ck(cudaError_t e) {
-  if (e != cudaSuccess) throw CudaError{e};
+thread_local char g_err_detail[256] = "";
+
+void ck_at(cudaError_t e, int line) {
+  if (e != cudaSuccess) {
+    snprintf(g_err_detail, sizeof(g_err_detail), "%s (%d) at driver.cu:%d", cudaGetErrorString(e), (int)e, line);
+    cudaGetLastError();
+    throw CudaError{e};
+  }
+}
+#define ck(x) ck_at((x), __LINE__)
+
+int PhaseTimer::begin(cudaStream_t st, int phase) {
+  if (!on || depth > 0) return -1;
+  ++depth;
+  size_t i = used++;
+  if (pool.size() < 2 * used) {
+    cudaEvent_t a, b;
+    ck(cudaEventCreate(&a));
+    ck(cudaEventCreate(&b));
+    pool.push_back(a);
+    pool.push_back(b);
+    phase_of.push_back(phase);
+  }
+  phase_of[i] = phase;
+  ck(cudaEventRecord(pool[2 * i], st));
+  return (int)i;
+}
+
+void PhaseTimer::end(cudaStream_t st, int token) {
+  if (token < 0) return;
+  --depth;
+  ck(cudaEventRecord(pool[2 * token + 1], st));
+}
+
+void PhaseTimer::flush() {
+  if (depth > 0) return;  // a bracket is still open: its end event is not recorded yet
+  for (size_t i = 0; i < used; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) ms[phase_of[i]] += t;
+  }
+  used = 0;
+}
+
+PhaseTimer::~PhaseTimer() {
+  for (auto e : pool) cudaEventDestroy(e);
 }
 
 void init_kernel_attributes() {
@@ -162,6 +205,7 @@ Solver::Solver(const schur_opts* o) {
     memcpy(&opts, o, sz);
   }
   st = (cudaStream_t)opts.stream;
+  timer.on = opts.timing != 0;
   if (opts.nmin <= 0) opts.nmin = 75;
   if (opts.nmin > NW_SMEM_MAX) opts.nmin = NW_SMEM_MAX;
   if (opts.nibble <= 0) opts.nibble = 14;
@@ -189,12 +233,14 @@ int Solver::setup(int n) {
     base = (char*)owned;
   }
   carve(base, n);
+  for (auto& L : levels) ck(cudaMemsetAsync(L.ctl, 0, sizeof(Ctl), st));
   return SCHUR_OK;
 }
 
 void Solver::read_ctl(const Ctl* dctl) {
   ck(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   ck(cudaStreamSynchronize(st));
+  timer.flush();
 }
 
 DeflParams Solver::defl(int n) const {
@@ -235,7 +281,11 @@ void Solver::run_updates(std::vector<UpdTask>& tasks) {
     size_t smem = apply_u_smem_bytes(tn, maxL);
     int per_sm = std::max(1, (int)((226 * 1024) / std::max<size_t>(smem, 1)));
     int grid = std::min(tile, num_sms() * std::min(per_sm, 8));
+    int tok = timer.begin(st, cur_update_phase);
+    ++g_stats.kernel_launches;
     ck(launch_apply_u(tn, grid, smem, st, a));
+    timer.end(st, tok);
+    if (cur_update_phase == PH_UPDATE && timer.depth == 0 && count_launches) g_stats.update_launches += 1;
   }
 }
 
@@ -329,9 +379,14 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
     }
     if (na == 0) continue;
     a.nchain = na;
+    int tok = timer.begin(st, PH_CHASE);
+    ++g_stats.kernel_launches;
     k_chase<<<na, CTA_THREADS, smem, st>>>(M.H, M.ldh, dpairs, Lv.ubuf, a);
     ck(cudaGetLastError());
+    timer.end(st, tok);
     g_stats.window_launches += 1;
+    if (lev == 0) g_stats.chase_launches += 1;
+    count_launches = (lev == 0);
     std::vector<UpdTask> t1, t2;
     for (int i = 0; i < na; ++i) {
       const ChainDesc& d = a.c[i];
@@ -366,6 +421,7 @@ int Solver::qr_block(const Mat3& M, int lev, int ilo, int ihi) {
   int it = 0;
   int ndfl = 1;
   while (kbot >= ilo) {
+    ++g_stats.kernel_launches;
     k_scan<<<1, CTA_THREADS, 0, st>>>(M.H, M.ldh, ilo, kbot, dp, Lv.ctl);
     ck(cudaGetLastError());
     read_ctl(Lv.ctl);
@@ -377,6 +433,7 @@ int Solver::qr_block(const Mat3& M, int lev, int ilo, int ihi) {
       continue;
     }
     if (m == 2) {
+      ++g_stats.kernel_launches;
       k_std2<<<1, CTA_THREADS, 0, st>>>(M.H, M.ldh, M.n, M.Z, M.ldz, M.Z ? M.zrows : 0, ktop);
       ck(cudaGetLastError());
       kbot -= 2;
@@ -385,9 +442,12 @@ int Solver::qr_block(const Mat3& M, int lev, int ilo, int ihi) {
     }
     if (m <= opts.nmin) {
       size_t smem = (size_t)(m | 1) * m * sizeof(double);
+      int tok = timer.begin(st, PH_SMALL);
+      ++g_stats.kernel_launches;
       k_smallqr<<<1, CTA_THREADS, smem, st>>>(M.H, M.ldh, ktop, kbot, Lv.usmall, m, dp, Lv.ctl);
       ck(cudaGetLastError());
       apply_block_transform(M, ktop, m, Lv.usmall, m, nullptr);
+      timer.end(st, tok);
       read_ctl(Lv.ctl);
       if (lev == 0) g_stats.small_qr += 1;
       if (hctl->info) return hctl->info;
@@ -431,12 +491,15 @@ int Solver::aed(const Mat3& M, int lev, int ktop, int kbot, int nw, int ns_max, 
   int kwtop = kbot - nw + 1;
   double* saved = cur_flops;
   if (lev == 0) cur_flops = &g_stats.aed_gemm_flops;
+  int tok = timer.begin(st, PH_AED);
   if (nw <= NW_SMEM_MAX) {
     size_t smem = (size_t)(nw | 1) * nw * sizeof(double);
+    ++g_stats.kernel_launches;
     k_aed_small<<<1, CTA_THREADS, smem, st>>>(M.H, M.ldh, ktop, kbot, nw, Lv.V, nw, Lv.cand_re, Lv.cand_im, Lv.vbuf,
                                              dp, dpw, Lv.ctl);
     ck(cudaGetLastError());
   } else {
+    ++g_stats.kernel_launches;
     k_copy_window<<<std::min(nw, 4 * num_sms()), CTA_THREADS, 0, st>>>(M.H, M.ldh, kwtop, nw, Lv.T, nw, Lv.V, nw);
     ck(cudaGetLastError());
     Mat3 W{Lv.T, nw, nw, Lv.V, nw, nw};
@@ -444,11 +507,17 @@ int Solver::aed(const Mat3& M, int lev, int ktop, int kbot, int nw, int ns_max, 
     cur_flops = nullptr;
     int inner = qr_block(W, lev + 1, 0, nw - 1);
     cur_flops = keep;
+    ++g_stats.kernel_launches;
     k_aed_big_post<<<1, CTA_THREADS, 0, st>>>(M.H, M.ldh, ktop, kbot, nw, Lv.T, nw, Lv.V, nw, Lv.cand_re, Lv.cand_im,
                                               Lv.vbuf, dp, Lv.ctl, inner);
     ck(cudaGetLastError());
   }
+  timer.end(st, tok);
+  int saved_phase = cur_update_phase;
+  cur_update_phase = PH_AED_UPDATE;
   apply_block_transform(M, kwtop, nw, Lv.V, nw, &Lv.ctl->nd);
+  cur_update_phase = saved_phase;
+  ++g_stats.kernel_launches;
   k_make_pairs<<<1, 32, 0, st>>>(M.H, M.ldh, ktop, kbot, std::min(ns_max, Lv.nsmax + 8 - 4), ndfl, 6, Lv.cand_re,
                                  Lv.cand_im, Lv.pairs, Lv.ctl);
   ck(cudaGetLastError());
@@ -488,6 +557,8 @@ extern "C" int schur_workspace_size(int n, const schur_opts* opts, size_t* bytes
   return SCHUR_OK;
 }
 
+extern "C" const char* schur_last_error_detail(void) { return g_err_detail; }
+
 extern "C" int schur_last_stats(schur_stats* out) {
   if (!out) return -1;
   *out = g_stats;
@@ -515,6 +586,7 @@ extern "C" int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, d
     if (rc) return rc;
     ck(cudaMemsetAsync(s.flag, 0, sizeof(int), s.st));
     int grid = std::min(n, 8 * num_sms());
+    ++g_stats.kernel_launches;
     k_prep<<<grid, CTA_THREADS, 0, s.st>>>(H, ldh, n, Z, ldz, s.opts.z_init, s.flag);
     ck(cudaGetLastError());
     int hflag = 0;
@@ -528,9 +600,19 @@ extern "C" int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, d
     Mat3 M{H, ldh, n, Z, ldz, n};
     s.cur_flops = &g_stats.sweep_gemm_flops;
     int info = s.qr_block(M, 0, 0, n - 1);
+    ++g_stats.kernel_launches;
     k_extract_eigs<<<std::max(1, std::min((n + 255) / 256, 4 * num_sms())), 256, 0, s.st>>>(H, ldh, n, wr, wi);
     ck(cudaGetLastError());
     ck(cudaStreamSynchronize(s.st));
+    s.timer.flush();
+    s.read_ctl(s.levels[0].ctl);
+    g_stats.aed_cycles_schur = (double)s.hctl->cyc_schur;
+    g_stats.aed_cycles_post = (double)s.hctl->cyc_defl;
+    g_stats.t_chase_ms = s.timer.ms[PH_CHASE];
+    g_stats.t_update_ms = s.timer.ms[PH_UPDATE];
+    g_stats.t_aed_ms = s.timer.ms[PH_AED];
+    g_stats.t_aed_update_ms = s.timer.ms[PH_AED_UPDATE];
+    g_stats.t_small_ms = s.timer.ms[PH_SMALL];
     return info;
   } catch (const CudaError&) {
     return SCHUR_ERR_CUDA;
@@ -652,6 +734,7 @@ extern "C" int schur_small_qr(int n, double* H, int ldh, double* Z, int ldz, int
     Mat3 M{H, ldh, n, Z, ldz, n};
     DeflParams dp = s.defl(n);
     size_t smem = (size_t)(m | 1) * m * sizeof(double);
+    ++g_stats.kernel_launches;
     k_smallqr<<<1, CTA_THREADS, smem, s.st>>>(H, ldh, ilo, ihi, s.levels[0].usmall, m, dp, s.levels[0].ctl);
     ck(cudaGetLastError());
     s.apply_block_transform(M, ilo, m, s.levels[0].usmall, m, nullptr);
@@ -684,4 +767,16 @@ extern "C" int schur_apply_u(int side, double* A, int lda, int r0, int c0, int m
   } catch (const CudaError&) {
     return SCHUR_ERR_CUDA;
   }
+}
+
+extern "C" int schur_fastmath_eval(int n, const double* x, double* out, const schur_opts* opts) {
+  if (n < 0) return -1;
+  if (n > 0 && !x) return -2;
+  if (n > 0 && !out) return -3;
+  if (n == 0) return SCHUR_OK;
+  cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
+  k_fastmath_eval<<<std::min((n + 255) / 256, 1024), 256, 0, st>>>(n, x, out);
+  if (cudaGetLastError() != cudaSuccess) return SCHUR_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SCHUR_ERR_CUDA;
+  return SCHUR_OK;
 }

@@ -42,6 +42,22 @@ struct Level {
   double* usmall = nullptr;
 };
 
+// Per-phase device timing with CUDA events (opts.timing = 1).
+enum Phase { PH_CHASE = 0, PH_UPDATE = 1, PH_AED = 2, PH_AED_UPDATE = 3, PH_SMALL = 4, PH_COUNT = 5 };
+
+struct PhaseTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> phase_of;   // phase of event pair i
+  size_t used = 0;             // event pairs recorded since the last flush
+  int depth = 0;               // > 0 while inside a timed region (nested launches not timed)
+  double ms[PH_COUNT] = {0, 0, 0, 0, 0};
+  int begin(cudaStream_t st, int phase);
+  void end(cudaStream_t st, int token);
+  void flush();                // after a stream synchronisation
+  ~PhaseTimer();
+};
+
 struct Solver {
   schur_opts opts;
   cudaStream_t st = nullptr;
@@ -50,6 +66,9 @@ struct Solver {
   int* flag = nullptr;
   double normH = 0.0;
   double* cur_flops = nullptr;
+  int cur_update_phase = PH_UPDATE;
+  bool count_launches = false;
+  PhaseTimer timer;
   std::vector<Level> levels;
 
   explicit Solver(const schur_opts* o);
@@ -66,6 +85,8 @@ struct Solver {
 };
 
 extern thread_local schur_stats g_stats;
+extern thread_local char g_err_detail[256];
+void ck_at(cudaError_t e, int line);
 void init_kernel_attributes();
 int num_sms();
 void default_ns_nw(int m, int* ns, int* nw);

@@ -113,9 +113,12 @@ __global__ void __launch_bounds__(CTA_THREADS) k_aed_small(double* H, long long 
     }
   double s = (kwtop > ktop) ? H[kwtop + (long long)(kwtop - 1) * ldh] : 0.0;
   __syncthreads();
+  long long c0 = clock64();
   int info = cta_francis(T, nw, 0, nw - 1, Vm, nw, dpw, &sh);
+  if (threadIdx.x == 0) ctl->cyc_schur += clock64() - c0;
   double top;
-  int nd = cta_aed_post(T, nw, info, s, Vm, dp, vbuf, cand_re, cand_im, &s_ncand, &top, &s_swf, &sh);
+  int nd = cta_aed_post(T, nw, info, s, Vm, dp, vbuf, cand_re, cand_im, &s_ncand, &top, &s_swf, &sh,
+                        &ctl->cyc_defl);
   if (nd > 0) aed_write_back(H, ldh, ktop, kwtop, nw, T, top);
   if (threadIdx.x == 0) {
     ctl->nd = nd;
@@ -148,7 +151,8 @@ __global__ void __launch_bounds__(CTA_THREADS) k_aed_big_post(double* H, long lo
   int info = inner_info;
   double s = (kwtop > ktop) ? H[kwtop + (long long)(kwtop - 1) * ldh] : 0.0;
   double top;
-  int nd = cta_aed_post(Tm, nw, info, s, Vm, dp, vbuf, cand_re, cand_im, &s_ncand, &top, &s_swf, &sh);
+  int nd = cta_aed_post(Tm, nw, info, s, Vm, dp, vbuf, cand_re, cand_im, &s_ncand, &top, &s_swf, &sh,
+                        &ctl->cyc_defl);
   __syncthreads();
   if (nd > 0) aed_write_back(H, ldh, ktop, kwtop, nw, Tm, top);
   if (threadIdx.x == 0) {
@@ -524,5 +528,18 @@ __global__ void k_extract_eigs(const double* H, long long ldh, int n, double* wr
       wr[j] = (j == s) ? r1 : r2;
       wi[j] = (j == s) ? i1 : i2;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostic: the low-latency reciprocal / reciprocal square root of
+// fastmath.cuh next to CUDA's IEEE division and square root.
+__global__ void k_fastmath_eval(int n, const double* x, double* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double v = x[i];
+    out[4 * i + 0] = fast_rcp(v);
+    out[4 * i + 1] = 1.0 / v;
+    out[4 * i + 2] = (v > 0.0) ? fast_rsqrt(v) : 0.0;
+    out[4 * i + 3] = (v > 0.0) ? 1.0 / sqrt(v) : 0.0;
   }
 }
