@@ -318,7 +318,7 @@ def main():
         "flops": {"reflector_algorithmic": st["reflector_flops"], "sweep_gemm_executed": st["sweep_gemm_flops"],
                   "aed_gemm_executed": st["aed_gemm_flops"]},
         "check": {"residual_probe": resid, "orthogonality_probe": orth, "trace_rel_err": trace_err},
-        "context": "paper (Table 4, L1280): syn_20000 StarNEig 68 s on 25 Skylake cores (different matrix family)",
+        "context": "paper Table 4: syn_20000 StarNEig 68 s on 25 Skylake cores (different matrix family)",
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -165,6 +165,16 @@ int schur_hessenberg_batched(int batch, const int* n, double* const* H, const in
                              const schur_opts* opts);
 
 /*
+ * schur_batched_set_table -- per-size-bucket (shifts, AED window) table used by
+ * schur_hessenberg_batched on this host thread (the autotuner's output; not
+ * in the paper).  Bucket b covers active blocks of at most max_n[b] rows (the
+ * last bucket covers all larger ones); 2 <= ns[b] <= 64, 4 <= nw[b] <= 128.
+ * nbuckets = 0 restores the built-in table.  All arrays are host arrays of
+ * nbuckets entries (nbuckets <= 8).
+ */
+int schur_batched_set_table(int nbuckets, const int* max_n, const int* ns, const int* nw);
+
+/*
  * schur_eig_backward -- adjoint of the eigenvalues (not in the paper).  For
  * a real loss L(lambda_1..lambda_n) with cotangents g_k = dL/dRe(lambda_k) +
  * i dL/dIm(lambda_k), returns dL/dH = Z G Z^T with

@@ -92,6 +92,7 @@ _SIGS = {
     "schur_apply_u": (c_int, [c_int, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_int,
                               P(SchurOpts)]),
     "schur_fastmath_eval": (c_int, [c_int, c_void_p, c_void_p, P(SchurOpts)]),
+    "schur_batched_set_table": (c_int, [c_int, P(c_int), P(c_int), P(c_int)]),
 }
 
 _LIB = None

@@ -143,3 +143,106 @@ def apply_u(side, A, r0, c0, m, U):
     o = _lib.make_opts(_stream_ptr().value)
     rc = lib.schur_apply_u(side, A.data_ptr(), _ld(A), r0, c0, m, k, U.data_ptr(), _ld(U), ctypes.byref(o))
     _check(rc, "schur_apply_u")
+
+
+def _ptrs(ts):
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() if t is not None else None for t in ts])
+
+
+def _ints(xs):
+    return (ctypes.c_int * len(xs))(*[int(x) for x in xs])
+
+
+def schur_batched_inplace(Hs, Zs, wrs, wis, z_init=0, deflation="lapack", fixed_thold=0.0):
+    """One persistent launch over column-major buffers (lists of tensors),
+    in place; returns the per-matrix info list."""
+    lib = _lib.load()
+    b = len(Hs)
+    info = (ctypes.c_int * max(b, 1))()
+    o = _lib.make_opts(_stream_ptr().value, z_init=z_init, deflation=deflation, fixed_thold=fixed_thold)
+    rc = lib.schur_hessenberg_batched(b, _ints([h.shape[0] for h in Hs]), _ptrs(Hs), _ints([_ld(h) for h in Hs]),
+                                      _ptrs(Zs), _ints([_ld(z) for z in Zs]), _ptrs(wrs), _ptrs(wis), info,
+                                      ctypes.byref(o))
+    _check(rc, "schur_hessenberg_batched")
+    return [info[i] for i in range(b)]
+
+
+def schur_batched(Hs, **kw):
+    """Batched reduction of a list of upper Hessenberg float64 CUDA tensors;
+    returns (S list, Z list, wr list, wi list, info list); inputs untouched."""
+    Ss = [colmajor(h.detach()).clone() for h in Hs]
+    Zs = [new_colmajor(h.shape[0], device=h.device) for h in Hs]
+    wrs = [torch.empty(h.shape[0], dtype=torch.float64, device=h.device) for h in Hs]
+    wis = [torch.empty(h.shape[0], dtype=torch.float64, device=h.device) for h in Hs]
+    info = schur_batched_inplace(Ss, Zs, wrs, wis, **kw)
+    return Ss, Zs, wrs, wis, info
+
+
+def set_batched_table(max_n, ns, nw):
+    """Per-size-bucket (shifts, window) table of the batched path ([] resets)."""
+    lib = _lib.load()
+    _check(lib.schur_batched_set_table(len(max_n), _ints(max_n), _ints(ns), _ints(nw)), "schur_batched_set_table")
+
+
+# ---------------------------------------------------------------------------
+# Backward (eigenvalue adjoint) and autograd
+# ---------------------------------------------------------------------------
+def eig_backward(S, Z, wr, wi, gwr, gwi):
+    """dL/dH = Z G Z^T for eigenvalue cotangents (gwr, gwi), S and Z from
+    ``schur``; returns a column-major n x n tensor."""
+    lib = _lib.load()
+    n = S.shape[0]
+    S = colmajor(S.detach())
+    Z = colmajor(Z.detach())
+    dH = new_colmajor(n, device=S.device)
+    o = _lib.make_opts(_stream_ptr().value)
+    rc = lib.schur_eig_backward(n, S.data_ptr(), _ld(S), Z.data_ptr(), _ld(Z), wr.data_ptr(), wi.data_ptr(),
+                                gwr.contiguous().data_ptr(), gwi.contiguous().data_ptr(), dH.data_ptr(), _ld(dH),
+                                ctypes.byref(o))
+    _check(rc, "schur_eig_backward")
+    return dH
+
+
+def eig_backward_batched(Ss, Zs, wrs, wis, gwrs, gwis):
+    lib = _lib.load()
+    b = len(Ss)
+    Ss = [colmajor(s.detach()) for s in Ss]
+    Zs = [colmajor(z.detach()) for z in Zs]
+    gwrs = [g.contiguous() for g in gwrs]
+    gwis = [g.contiguous() for g in gwis]
+    dHs = [new_colmajor(s.shape[0], device=s.device) for s in Ss]
+    o = _lib.make_opts(_stream_ptr().value)
+    rc = lib.schur_eig_backward_batched(b, _ints([s.shape[0] for s in Ss]), _ptrs(Ss), _ints([_ld(s) for s in Ss]),
+                                        _ptrs(Zs), _ints([_ld(z) for z in Zs]), _ptrs(wrs), _ptrs(wis),
+                                        _ptrs(gwrs), _ptrs(gwis), _ptrs(dHs), _ints([_ld(d) for d in dHs]),
+                                        ctypes.byref(o))
+    _check(rc, "schur_eig_backward_batched")
+    return dHs
+
+
+class Eigvals(torch.autograd.Function):
+    """(wr, wi) = eigenvalues of the upper Hessenberg part of H; backward maps
+    (dL/dwr, dL/dwi) to dL/dH through the library's adjoint.  Entries below
+    the first subdiagonal do not enter the reduction, so their gradient is
+    zero."""
+
+    @staticmethod
+    def forward(ctx, H):
+        S, Z, wr, wi, rc = schur(H)
+        if rc != 0:
+            raise RuntimeError(f"schur_hessenberg returned {rc}")
+        ctx.save_for_backward(S, Z, wr, wi)
+        return wr.clone(), wi.clone()
+
+    @staticmethod
+    def backward(ctx, gwr, gwi):
+        S, Z, wr, wi = ctx.saved_tensors
+        n = S.shape[0]
+        gwr = torch.zeros(n, dtype=torch.float64, device=S.device) if gwr is None else gwr
+        gwi = torch.zeros(n, dtype=torch.float64, device=S.device) if gwi is None else gwi
+        dH = eig_backward(S, Z, wr, wi, gwr, gwi)
+        return torch.triu(dH, diagonal=-1)
+
+
+def eigvals(H):
+    return Eigvals.apply(H)

@@ -1,11 +1,548 @@
-// adjoint.cu -- placeholder until the adjoint kernels land.
+// adjoint.cu -- eigenvalue adjoint dL/dH (not in the paper).
+//
+// For cotangents g_k = dL/dRe(lambda_k) + i dL/dIm(lambda_k), first-order
+// perturbation theory (d lambda = y^H dH x / y^H x) gives
+//     dL/dH = Z G Z^T,   G = Re( sum_k conj(g_k) / c_k  w_k x_k^T ),
+// with x_k, w_k = conj(y_k) the right eigenvectors of S and of S^T
+// (S x = lambda x, S^T w = lambda w) and c_k = w_k^T x_k.  For a complex pair
+// (lambda, conj(lambda)) the two terms combine into
+//     Re( (conj(g_k) + g_{k+1}) / c_k  w_k x_k^T )
+// (the partner's vectors are the conjugates), so one complex vector pair per
+// diagonal block is computed:
+//   * k_adj_vectors: one warp per diagonal block; x by block back
+//     substitution in column (axpy) order -- after x_j is final, column j of
+//     S updates the right-hand sides above it, reading S contiguously --; w by
+//     forward substitution with the dot products over contiguous columns of
+//     S; c = w_b^T x_b involves the block rows only.  Writes
+//     XR = Re x, XI = Im x, P = Re(e w), Q = Im(e w) with e the coefficient
+//     above (zero columns for the second row of a pair).
+//   * k_gemm: G = P XR^T - Q XI^T, T = Z G, dH = T Z^T (FP64 FFMA tiles).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "../../include/schur_gb300.h"
-extern "C" int schur_eig_backward(int, const double*, int, const double*, int, const double*, const double*,
-                                  const double*, const double*, double*, int, const schur_opts*) {
-  return SCHUR_ERR_UNSUPPORTED;
+#include "common.cuh"
+#include "host.h"
+
+#define ADJ_WARPS 8          // warps (vector blocks) per thread block
+#define ADJ_NMAX 1024
+
+struct AdjDesc {
+  const double* S;
+  const double* Z;
+  const double* wr;
+  const double* wi;
+  const double* gwr;
+  const double* gwi;
+  double* dH;
+  double* ws;         // 5 n^2 doubles: XR, XI, P, Q, T (each n x n, ld n)
+  long long lds, ldz, lddh;
+  int n;
+  int item0;          // first global item (= eigenvalue index) of this matrix
+};
+
+// complex helpers (pairs of doubles)
+struct cplx {
+  double r, i;
+};
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {fma(a.r, b.r, -a.i * b.i), fma(a.r, b.i, a.i * b.r)}; }
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b, double smin2) {
+  double d = fma(b.r, b.r, b.i * b.i);
+  if (d < smin2) d = smin2;  // perturbation of a (nearly) repeated eigenvalue
+  double rd = fast_rcp(d);
+  return {fma(a.r, b.r, a.i * b.i) * rd, fma(a.i, b.r, -a.r * b.i) * rd};
 }
-extern "C" int schur_eig_backward_batched(int, const int*, double* const*, const int*, double* const*, const int*,
-                                          double* const*, double* const*, double* const*, double* const*,
-                                          double* const*, const int*, const schur_opts*) {
-  return SCHUR_ERR_UNSUPPORTED;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_absmax(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Solve (B - lam I) x = r for the 1x1 / 2x2 real block B (transposed when
+// trans), complex lam and r.
+__device__ inline void block_solve(int sz, const double* B, bool trans, cplx lam, const cplx* r, cplx* x,
+                                   double smin2) {
+  if (sz == 1) {
+    x[0] = cdiv(r[0], cplx{B[0] - lam.r, -lam.i}, smin2);
+    return;
+  }
+  // B column-major 2x2: B[0]=b00, B[1]=b10, B[2]=b01, B[3]=b11
+  double b00 = B[0], b10 = trans ? B[2] : B[1], b01 = trans ? B[1] : B[2], b11 = B[3];
+  cplx m00{b00 - lam.r, -lam.i}, m11{b11 - lam.r, -lam.i};
+  cplx det = cmul(m00, m11);
+  det.r -= b01 * b10;
+  cplx n0 = cmul(m11, r[0]);
+  n0.r -= b01 * r[1].r;
+  n0.i -= b01 * r[1].i;
+  cplx n1 = cmul(m00, r[1]);
+  n1.r -= b10 * r[0].r;
+  n1.i -= b10 * r[0].i;
+  x[0] = cdiv(n0, det, smin2);
+  x[1] = cdiv(n1, det, smin2);
+}
+
+// ---------------------------------------------------------------------------
+// One warp per eigenvalue index k (global item); the warp of the second row
+// of a 2x2 block writes zero columns.  Per-warp shared buffer of 2 n doubles.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32 * ADJ_WARPS) k_adj_vectors(const AdjDesc* __restrict__ descs, int ndesc,
+                                                               int nitems, int nst) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int item = blockIdx.x * ADJ_WARPS + warp;
+  if (item >= nitems) return;
+  int b = 0;
+  {
+    int lo = 0, hi = ndesc - 1;  // last descriptor with item0 <= item
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (descs[mid].item0 <= item) lo = mid; else hi = mid - 1;
+    }
+    b = lo;
+  }
+  const AdjDesc& d = descs[b];
+  const int n = d.n;
+  const int k = item - d.item0;
+  if (k < 0 || k >= n) return;
+  Mat S{const_cast<double*>(d.S), d.lds};
+  const long long nn = (long long)n * n;
+  double* XR = d.ws;
+  double* XI = XR + nn;
+  double* PP = XI + nn;
+  double* QQ = PP + nn;
+  double* xr = smem + (size_t)warp * 2 * nst;
+  double* xi = xr + nst;
+  const bool second = (k > 0 && S(k, k - 1) != 0.0);
+  if (second) {
+    for (int r = lane; r < n; r += 32) {
+      XR[r + (long long)k * n] = 0.0;
+      XI[r + (long long)k * n] = 0.0;
+      PP[r + (long long)k * n] = 0.0;
+      QQ[r + (long long)k * n] = 0.0;
+    }
+    return;
+  }
+  const int sz = (k + 1 < n && S(k + 1, k) != 0.0) ? 2 : 1;
+  const cplx lam{d.wr[k], (sz == 2) ? d.wi[k] : 0.0};
+  // smallest pivot: u * max |S_jj| (perturbation of repeated eigenvalues)
+  double smax = 0.0;
+  for (int r = lane; r < n; r += 32) smax = fmax(smax, fabs(S(r, r)));
+  smax = warp_absmax(smax);
+  double smin = fmax(SCHUR_U * smax, 1e-290);
+  double smin2 = smin * smin;
+  double Bk[4] = {S(k, k), (sz == 2) ? S(k + 1, k) : 0.0, (sz == 2) ? S(k, k + 1) : 0.0,
+                  (sz == 2) ? S(k + 1, k + 1) : 0.0};
+  // ---- right vector: block part, then back substitution upward
+  for (int r = lane; r < n; r += 32) {
+    xr[r] = 0.0;
+    xi[r] = 0.0;
+  }
+  __syncwarp();
+  cplx xb[2];
+  if (sz == 1) {
+    xb[0] = {1.0, 0.0};
+  } else {
+    double a = Bk[0], bb = Bk[2], c = Bk[1], dd = Bk[3];
+    cplx u0{bb, 0.0}, u1{lam.r - a, lam.i};
+    if (fabs(u0.r) + fabs(u1.r) + fabs(u1.i) == 0.0) {
+      u0 = {lam.r - dd, lam.i};
+      u1 = {c, 0.0};
+    }
+    xb[0] = u0;
+    xb[1] = u1;
+  }
+  // rhs rows < k from the block's columns
+  for (int t = 0; t < sz; ++t) {
+    const double* col = &S(0, k + t);
+    for (int r = lane; r < k; r += 32) {
+      xr[r] = fma(-col[r], xb[t].r, xr[r]);
+      xi[r] = fma(-col[r], xb[t].i, xi[r]);
+    }
+  }
+  if (lane == 0) {
+    for (int t = 0; t < sz; ++t) {
+      xr[k + t] = xb[t].r;
+      xi[k + t] = xb[t].i;
+    }
+  }
+  __syncwarp();
+  int j = k - 1;
+  while (j >= 0) {
+    int bs = (j >= 1 && S(j, j - 1) != 0.0) ? 2 : 1;
+    int j0 = j - bs + 1;
+    cplx xs[2];
+    if (lane == 0) {
+      double B[4] = {S(j0, j0), (bs == 2) ? S(j0 + 1, j0) : 0.0, (bs == 2) ? S(j0, j0 + 1) : 0.0,
+                     (bs == 2) ? S(j0 + 1, j0 + 1) : 0.0};
+      cplx rr[2] = {{xr[j0], xi[j0]}, {(bs == 2) ? xr[j0 + 1] : 0.0, (bs == 2) ? xi[j0 + 1] : 0.0}};
+      block_solve(bs, B, false, lam, rr, xs, smin2);
+      for (int t = 0; t < bs; ++t) {
+        xr[j0 + t] = xs[t].r;
+        xi[j0 + t] = xs[t].i;
+      }
+    }
+    __syncwarp();
+    for (int t = 0; t < bs; ++t) {
+      double vr = xr[j0 + t], vi = xi[j0 + t];
+      const double* col = &S(0, j0 + t);
+      for (int r = lane; r < j0; r += 32) {
+        xr[r] = fma(-col[r], vr, xr[r]);
+        xi[r] = fma(-col[r], vi, xi[r]);
+      }
+    }
+    __syncwarp();
+    j = j0 - 1;
+  }
+  // normalise by max |x| and store
+  double mx = 0.0;
+  for (int r = lane; r < k + sz; r += 32) mx = fmax(mx, fmax(fabs(xr[r]), fabs(xi[r])));
+  mx = warp_absmax(mx);
+  double rs = (mx > 0.0) ? fast_rcp(mx) : 1.0;
+  for (int r = lane; r < n; r += 32) {
+    bool in = r < k + sz;
+    XR[r + (long long)k * n] = in ? xr[r] * rs : 0.0;
+    XI[r + (long long)k * n] = in ? xi[r] * rs : 0.0;
+  }
+  cplx xbs[2] = {{xr[k] * rs, xi[k] * rs}, {(sz == 2) ? xr[k + 1] * rs : 0.0, (sz == 2) ? xi[k + 1] * rs : 0.0}};
+  __syncwarp();
+  // ---- left vector (S^T w = lam w): block part, forward substitution
+  for (int r = lane; r < n; r += 32) {
+    xr[r] = 0.0;
+    xi[r] = 0.0;
+  }
+  __syncwarp();
+  cplx wb[2];
+  if (sz == 1) {
+    wb[0] = {1.0, 0.0};
+  } else {
+    double a = Bk[0], bb = Bk[2], c = Bk[1], dd = Bk[3];
+    cplx u0{c, 0.0}, u1{lam.r - a, lam.i};
+    if (fabs(u0.r) + fabs(u1.r) + fabs(u1.i) == 0.0) {
+      u0 = {lam.r - dd, lam.i};
+      u1 = {bb, 0.0};
+    }
+    wb[0] = u0;
+    wb[1] = u1;
+  }
+  if (lane == 0)
+    for (int t = 0; t < sz; ++t) {
+      xr[k + t] = wb[t].r;
+      xi[k + t] = wb[t].i;
+    }
+  __syncwarp();
+  j = k + sz;
+  while (j < n) {
+    int bs = (j + 1 < n && S(j + 1, j) != 0.0) ? 2 : 1;
+    cplx rr[2];
+    for (int t = 0; t < bs; ++t) {
+      const double* col = &S(0, j + t);
+      double sr = 0.0, si = 0.0;
+      for (int r = k + lane; r < j; r += 32) {
+        sr = fma(col[r], xr[r], sr);
+        si = fma(col[r], xi[r], si);
+      }
+      rr[t] = {-warp_sum(sr), -warp_sum(si)};
+    }
+    if (lane == 0) {
+      double B[4] = {S(j, j), (bs == 2) ? S(j + 1, j) : 0.0, (bs == 2) ? S(j, j + 1) : 0.0,
+                     (bs == 2) ? S(j + 1, j + 1) : 0.0};
+      cplx ws2[2];
+      block_solve(bs, B, true, lam, rr, ws2, smin2);
+      for (int t = 0; t < bs; ++t) {
+        xr[j + t] = ws2[t].r;
+        xi[j + t] = ws2[t].i;
+      }
+    }
+    __syncwarp();
+    j += bs;
+  }
+  mx = 0.0;
+  for (int r = k + lane; r < n; r += 32) mx = fmax(mx, fmax(fabs(xr[r]), fabs(xi[r])));
+  mx = warp_absmax(mx);
+  rs = (mx > 0.0) ? fast_rcp(mx) : 1.0;
+  // c = w_b^T x_b (block rows only); e = g_r / c (real) or
+  // (conj(g_k) + g_{k+1}) / c (pair)
+  cplx c{0.0, 0.0};
+  for (int t = 0; t < sz; ++t) {
+    cplx wv{xr[k + t] * rs, xi[k + t] * rs};
+    cplx p = cmul(wv, xbs[t]);
+    c.r += p.r;
+    c.i += p.i;
+  }
+  cplx num;
+  if (sz == 1) {
+    num = {d.gwr[k], 0.0};
+  } else {
+    num = {d.gwr[k] + d.gwr[k + 1], -d.gwi[k] + d.gwi[k + 1]};
+  }
+  cplx e = cdiv(num, c, 1e-300);
+  for (int r = lane; r < n; r += 32) {
+    bool in = r >= k;
+    cplx wv{in ? xr[r] * rs : 0.0, in ? xi[r] * rs : 0.0};
+    cplx ew = cmul(e, wv);
+    PP[r + (long long)k * n] = ew.r;
+    QQ[r + (long long)k * n] = ew.i;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched FP64 GEMM: C = alpha * A * op(B) + beta * C (column-major; op(B) =
+// B or B^T), 64 x 64 output tiles, K in chunks of 16 through shared memory,
+// 4 x 4 outputs per thread.
+// ---------------------------------------------------------------------------
+struct GemmTask {
+  const double* A;
+  const double* B;
+  double* C;
+  long long lda, ldb, ldc;
+  int M, N, K, transB;
+  double alpha, beta;
+  int tile0, tiles_n, ntile, pad;
+};
+
+__global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks, int ntask, int total) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    int lo = 0, hi = ntask - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (tasks[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+    }
+    const GemmTask& t = tasks[lo];
+    const int local = tile - t.tile0;
+    const int m0 = (local / t.tiles_n) * 64, n0 = (local % t.tiles_n) * 64;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int k0 = 0; k0 < t.K; k0 += 16) {
+      for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
+        int i = idx & 63, kk = idx >> 6;
+        int r = m0 + i, c = k0 + kk;
+        As[kk][i] = (r < t.M && c < t.K) ? t.A[r + (long long)c * t.lda] : 0.0;
+        int j, kb;
+        if (t.transB) {
+          j = idx & 63;
+          kb = idx >> 6;
+        } else {
+          kb = idx & 15;
+          j = idx >> 4;
+        }
+        int col = n0 + j, kr = k0 + kb;
+        double v = 0.0;
+        if (col < t.N && kr < t.K)
+          v = t.transB ? t.B[col + (long long)kr * t.ldb] : t.B[kr + (long long)col * t.ldb];
+        Bs[kb][j] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        int r = m0 + ty * 4 + a, c = n0 + tx * 4 + b;
+        if (r < t.M && c < t.N) {
+          double* cp = t.C + r + (long long)c * t.ldc;
+          *cp = (t.beta == 0.0) ? t.alpha * acc[a][b] : fma(t.alpha, acc[a][b], t.beta * *cp);
+        }
+      }
+  }
+}
+
+// ===========================================================================
+// Host side
+// ===========================================================================
+namespace {
+
+struct AdjMatrix {
+  int n;
+  const double *S, *Z, *wr, *wi, *gwr, *gwi;
+  double* dH;
+  int lds, ldz, lddh;
+};
+
+using schur::ck_at;
+using schur::CudaError;
+
+int run_backward(const std::vector<AdjMatrix>& ms, const schur_opts* opts) {
+  schur_opts o;
+  schur_default_opts(&o);
+  if (opts) memcpy(&o, opts, std::min((size_t)std::max(opts->struct_size, 0), sizeof(o)));
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const int nb = (int)ms.size();
+  size_t ws_doubles = 0;
+  int nmax = 1, items = 0;
+  for (auto& m : ms) {
+    ws_doubles += 5 * (size_t)m.n * m.n;
+    nmax = std::max(nmax, m.n);
+    items += m.n;
+  }
+  size_t desc_bytes = ((size_t)nb * sizeof(AdjDesc) + 255) & ~(size_t)255;
+  size_t task_bytes = ((size_t)4 * nb * sizeof(GemmTask) + 255) & ~(size_t)255;
+  size_t need = ws_doubles * sizeof(double) + desc_bytes + task_bytes;
+  char* mem = nullptr;
+  bool own = false;
+  int rc = SCHUR_OK;
+  try {
+    schur::init_kernel_attributes();
+    if (o.workspace && o.workspace_bytes >= need) {
+      mem = (char*)o.workspace;
+    } else if (o.workspace) {
+      return SCHUR_ERR_WORKSPACE;
+    } else {
+      if (cudaMalloc((void**)&mem, need) != cudaSuccess) {
+        cudaGetLastError();
+        return SCHUR_ERR_NOMEM;
+      }
+      own = true;
+    }
+    double* wsbase = (double*)mem;
+    std::vector<AdjDesc> hd(nb);
+    size_t off = 0;
+    int item0 = 0;
+    for (int b = 0; b < nb; ++b) {
+      const AdjMatrix& m = ms[b];
+      hd[b] = AdjDesc{m.S, m.Z, m.wr, m.wi, m.gwr, m.gwi, m.dH, wsbase + off, m.lds, m.ldz, m.lddh, m.n, item0};
+      off += 5 * (size_t)m.n * m.n;
+      item0 += m.n;
+    }
+    AdjDesc* ddesc = (AdjDesc*)(mem + ws_doubles * sizeof(double));
+    GemmTask* dtask = (GemmTask*)((char*)ddesc + desc_bytes);
+    ck_at(cudaMemcpyAsync(ddesc, hd.data(), nb * sizeof(AdjDesc), cudaMemcpyHostToDevice, st), __LINE__);
+    size_t smem = (size_t)ADJ_WARPS * 2 * nmax * sizeof(double);
+    ck_at(cudaFuncSetAttribute(k_adj_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), __LINE__);
+    k_adj_vectors<<<(items + ADJ_WARPS - 1) / ADJ_WARPS, 32 * ADJ_WARPS, smem, st>>>(ddesc, nb, items, nmax);
+    ck_at(cudaGetLastError(), __LINE__);
+    ++schur::g_stats.kernel_launches;
+    // three GEMM phases: G = P XR^T - Q XI^T (into T), W = Z G (into P),
+    // dH = W Z^T
+    std::vector<GemmTask> tasks;
+    auto add = [&](const double* A, long long lda, const double* B, long long ldb, double* C, long long ldc, int M,
+                   int N, int K, int transB, double alpha, double beta) {
+      GemmTask t;
+      memset(&t, 0, sizeof(t));
+      t.A = A; t.B = B; t.C = C; t.lda = lda; t.ldb = ldb; t.ldc = ldc;
+      t.M = M; t.N = N; t.K = K; t.transB = transB; t.alpha = alpha; t.beta = beta;
+      tasks.push_back(t);
+    };
+    auto launch = [&]() {
+      int tile = 0;
+      for (auto& t : tasks) {
+        t.tiles_n = (t.N + 63) / 64;
+        t.ntile = ((t.M + 63) / 64) * t.tiles_n;
+        t.tile0 = tile;
+        tile += t.ntile;
+      }
+      ck_at(cudaMemcpyAsync(dtask, tasks.data(), tasks.size() * sizeof(GemmTask), cudaMemcpyHostToDevice, st),
+            __LINE__);
+      k_gemm<<<std::min(tile, 4 * schur::num_sms()), 256, 0, st>>>(dtask, (int)tasks.size(), tile);
+      ck_at(cudaGetLastError(), __LINE__);
+      ++schur::g_stats.kernel_launches;
+      // the task array is reused by the next phase: wait for this one
+      ck_at(cudaStreamSynchronize(st), __LINE__);
+      tasks.clear();
+    };
+    for (int b = 0; b < nb; ++b) {
+      const AdjDesc& d = hd[b];
+      long long nn = (long long)d.n * d.n;
+      double *XR = d.ws, *XI = XR + nn, *PP = XI + nn, *QQ = PP + nn, *TT = QQ + nn;
+      add(PP, d.n, XR, d.n, TT, d.n, d.n, d.n, d.n, 1, 1.0, 0.0);
+    }
+    launch();
+    for (int b = 0; b < nb; ++b) {
+      const AdjDesc& d = hd[b];
+      long long nn = (long long)d.n * d.n;
+      double *XR = d.ws, *XI = XR + nn, *PP = XI + nn, *QQ = PP + nn, *TT = QQ + nn;
+      add(QQ, d.n, XI, d.n, TT, d.n, d.n, d.n, d.n, 1, -1.0, 1.0);
+    }
+    launch();
+    for (int b = 0; b < nb; ++b) {
+      const AdjDesc& d = hd[b];
+      long long nn = (long long)d.n * d.n;
+      double *PP = d.ws + 2 * nn, *TT = d.ws + 4 * nn;
+      add(d.Z, d.ldz, TT, d.n, PP, d.n, d.n, d.n, d.n, 0, 1.0, 0.0);
+    }
+    launch();
+    for (int b = 0; b < nb; ++b) {
+      const AdjDesc& d = hd[b];
+      long long nn = (long long)d.n * d.n;
+      double* PP = d.ws + 2 * nn;
+      add(PP, d.n, d.Z, d.ldz, d.dH, d.lddh, d.n, d.n, d.n, 1, 1.0, 0.0);
+    }
+    launch();
+  } catch (const CudaError&) {
+    rc = SCHUR_ERR_CUDA;
+  }
+  if (own && mem) cudaFree(mem);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int schur_eig_backward(int n, const double* S, int lds, const double* Z, int ldz, const double* wr,
+                                  const double* wi, const double* gwr, const double* gwi, double* dH, int lddh,
+                                  const schur_opts* opts) {
+  if (n < 0 || n > ADJ_NMAX) return -1;
+  if (n == 0) return SCHUR_OK;
+  if (!S) return -2;
+  if (lds < n) return -3;
+  if (!Z) return -4;
+  if (ldz < n) return -5;
+  if (!wr) return -6;
+  if (!wi) return -7;
+  if (!gwr) return -8;
+  if (!gwi) return -9;
+  if (!dH) return -10;
+  if (lddh < n) return -11;
+  std::vector<AdjMatrix> ms{AdjMatrix{n, S, Z, wr, wi, gwr, gwi, dH, lds, ldz, lddh}};
+  return run_backward(ms, opts);
+}
+
+extern "C" int schur_eig_backward_batched(int batch, const int* n, double* const* S, const int* lds, double* const* Z,
+                                          const int* ldz, double* const* wr, double* const* wi, double* const* gwr,
+                                          double* const* gwi, double* const* dH, const int* lddh,
+                                          const schur_opts* opts) {
+  if (batch < 0) return -1;
+  if (batch == 0) return SCHUR_OK;
+  if (!n) return -2;
+  if (!S || !lds) return -3;
+  if (!Z || !ldz) return -5;
+  if (!wr) return -7;
+  if (!wi) return -8;
+  if (!gwr) return -9;
+  if (!gwi) return -10;
+  if (!dH || !lddh) return -11;
+  std::vector<AdjMatrix> ms(batch);
+  for (int b = 0; b < batch; ++b) {
+    if (n[b] < 1 || n[b] > ADJ_NMAX) return -2;
+    if (!S[b] || lds[b] < n[b]) return -3;
+    if (!Z[b] || ldz[b] < n[b]) return -5;
+    if (!dH[b] || lddh[b] < n[b]) return -11;
+    ms[b] = AdjMatrix{n[b], S[b], Z[b], wr[b], wi[b], gwr[b], gwi[b], dH[b], lds[b], ldz[b], lddh[b]};
+  }
+  return run_backward(ms, opts);
 }

@@ -704,3 +704,62 @@ __device__ inline int cta_aed_post(const Mat& T, int nw, int info, double s, con
   }
   return nd;
 }
+
+// ---------------------------------------------------------------------------
+// Shift pairs for the next sweep (one thread).  Reading of Sec. 2.5: the
+// undeflated AED candidates become the shifts -- the bottom-most ones, complex
+// conjugates kept together, real shifts paired in order of appearance; an
+// exceptional pair every exc_period-th iteration without deflation
+// (ndfl % exc_period == 0); the trailing 2x2 when no candidate is left.
+// Writes (sum, product) pairs and returns their count (at most
+// min(ns_max, m - 1) / 2 for the active block [ktop, kbot] of m rows).
+// ---------------------------------------------------------------------------
+__device__ inline int make_shift_pairs(const Mat& H, int ktop, int kbot, int ns_max, int ndfl, int exc_period,
+                                       const double* cand_re, const double* cand_im, int ncand, double* pairs) {
+  int m = kbot - ktop + 1;
+  int ns = min(ns_max, m - 1);
+  ns -= ns % 2;
+  int want = ns / 2;
+  int np = 0;
+  if (m < 3 || want <= 0) return 0;
+  if (ndfl % exc_period == 0) {
+    for (int i = kbot; np < want && i > ktop; i -= 2) {
+      double ss, sp;
+      exceptional_pair(H, ktop, i, ss, sp);
+      pairs[2 * np] = ss;
+      pairs[2 * np + 1] = sp;
+      ++np;
+    }
+    return np;
+  }
+  bool pending = false;
+  double pv = 0.0;
+  int i = ncand - 1;
+  while (i >= 0 && np < want) {
+    double re = cand_re[i], im = cand_im[i];
+    if (im != 0.0) {
+      pairs[2 * np] = 2.0 * re;
+      pairs[2 * np + 1] = re * re + im * im;
+      ++np;
+      i -= 2;
+      continue;
+    }
+    if (!pending) {
+      pending = true;
+      pv = re;
+    } else {
+      pairs[2 * np] = pv + re;
+      pairs[2 * np + 1] = pv * re;
+      ++np;
+      pending = false;
+    }
+    i -= 1;
+  }
+  if (np == 0) {
+    double a = H(kbot - 1, kbot - 1), b = H(kbot - 1, kbot), c = H(kbot, kbot - 1), d = H(kbot, kbot);
+    pairs[0] = a + d;
+    pairs[1] = a * d - b * c;
+    np = 1;
+  }
+  return np;
+}

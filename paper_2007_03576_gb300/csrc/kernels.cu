@@ -174,56 +174,9 @@ __global__ void k_make_pairs(const double* H, long long ldh, int ktop, int kbot_
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Mat Hm{const_cast<double*>(H), ldh};
   int nd = ctl->nd;
-  int kbot = kbot_old - nd;
-  int m = kbot - ktop + 1;
   int ndfl = (nd > 0) ? 1 : ndfl_host + 1;
-  int ns = min(ns_max, m - 1);
-  ns -= ns % 2;
-  int want = ns / 2;
-  int np = 0;
-  if (m >= 3 && want > 0) {
-    if (ndfl % exc_period == 0) {
-      for (int i = kbot; np < want && i > ktop; i -= 2) {
-        double ss, sp;
-        exceptional_pair(Hm, ktop, i, ss, sp);
-        pairs[2 * np] = ss;
-        pairs[2 * np + 1] = sp;
-        ++np;
-      }
-    } else {
-      int nc = ctl->ncand;
-      bool pending = false;
-      double pv = 0.0;
-      int i = nc - 1;
-      while (i >= 0 && np < want) {
-        double re = cand_re[i], im = cand_im[i];
-        if (im != 0.0) {
-          pairs[2 * np] = 2.0 * re;
-          pairs[2 * np + 1] = re * re + im * im;
-          ++np;
-          i -= 2;
-          continue;
-        }
-        if (!pending) {
-          pending = true;
-          pv = re;
-        } else {
-          pairs[2 * np] = pv + re;
-          pairs[2 * np + 1] = pv * re;
-          ++np;
-          pending = false;
-        }
-        i -= 1;
-      }
-      if (np == 0) {
-        double a = Hm(kbot - 1, kbot - 1), b = Hm(kbot - 1, kbot), c = Hm(kbot, kbot - 1), d = Hm(kbot, kbot);
-        pairs[0] = a + d;
-        pairs[1] = a * d - b * c;
-        np = 1;
-      }
-    }
-  }
-  ctl->npairs = np;
+  ctl->npairs = make_shift_pairs(Hm, ktop, kbot_old - nd, ns_max, ndfl, exc_period, cand_re, cand_im, ctl->ncand,
+                                 pairs);
   ctl->ndfl = ndfl;
 }
 
