@@ -52,6 +52,7 @@ extern "C" {
 #define SCHUR_ERR_NOMEM (-1003)     /* scratch allocation failed */
 #define SCHUR_ERR_WORKSPACE (-1004) /* caller workspace too small */
 #define SCHUR_ERR_UNSUPPORTED (-1005)
+#define SCHUR_ERR_TOO_LARGE (-1006) /* order above the fixed limit of schur_hessenberg_noalloc */
 
 /* Deflation conditions of Sec. 5.6. */
 #define SCHUR_DEFLATION_LAPACK 0 /* item 1 (the paper's experiments) */
@@ -131,6 +132,30 @@ int schur_workspace_size(int n, const schur_opts* opts, size_t* bytes);
  */
 int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, double* wr, double* wi,
                      const schur_opts* opts);
+
+/*
+ * schur_hessenberg_noalloc -- schur_hessenberg for callers that cannot
+ * allocate memory during the call (no counterpart in the paper).  Examples:
+ * a host framework that owns every device allocation through its own pool,
+ * a real-time loop with a fixed memory budget, code that must avoid the
+ * implicit device synchronisation of cudaMalloc / cudaFree.  Arguments and
+ * results as in schur_hessenberg (device pointers; Z is required and is set
+ * to I on entry unless opts->z_init == 1; opts may be NULL).  One thread block
+ * reduces the matrix with the batched engine (AED windows of at most 64
+ * rows), so it suits small and medium orders.
+ *   - Allocates nothing: its scratch (about 37 KB) is a fixed array in
+ *     device memory that every device holding the library keeps until the
+ *     process exits.  The first call on a device looks up that array's
+ *     device address (the device must be current); make that first call
+ *     before any stream capture.
+ *   - n > 1024 returns SCHUR_ERR_TOO_LARGE without touching the device.
+ *   - All calls share the one array: calls that may overlap on the GPU
+ *     (different streams or host threads) race and must be serialised by
+ *     the caller.  Each call resets the parts that must start at zero.
+ *   - Synchronises opts->stream before returning (it returns the status).
+ */
+int schur_hessenberg_noalloc(int n, double* H, int ldh, double* Z, int ldz, double* wr, double* wi,
+                             const schur_opts* opts);
 
 /* Statistics of the last schur_hessenberg call made by this host thread. */
 int schur_last_stats(schur_stats* out);

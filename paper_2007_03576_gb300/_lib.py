@@ -24,6 +24,7 @@ SCHUR_ERR_CUDA = -1002
 SCHUR_ERR_NOMEM = -1003
 SCHUR_ERR_WORKSPACE = -1004
 SCHUR_ERR_UNSUPPORTED = -1005
+SCHUR_ERR_TOO_LARGE = -1006
 
 DEFLATION = {"lapack": 0, "norm": 1, "fixed": 2}
 
@@ -93,6 +94,8 @@ _SIGS = {
                               P(SchurOpts)]),
     "schur_fastmath_eval": (c_int, [c_int, c_void_p, c_void_p, P(SchurOpts)]),
     "schur_batched_set_table": (c_int, [c_int, P(c_int), P(c_int), P(c_int)]),
+    "schur_hessenberg_noalloc": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p,
+                                         P(SchurOpts)]),
 }
 
 _LIB = None

@@ -20,37 +20,7 @@
 #include "cta.cuh"
 #include "host.h"
 
-#define B_MAX_BUCKETS 8
-#define B_NW_MAX 128       // AED window limit of the batched engine
-#define B_STAGE_COLS 32    // vectors staged per chunk of a window product
-
-struct BatchedParams {
-  int nmin, nibble, mode, exc_period;
-  double thold;
-  int nbuckets;
-  int bucket_max_n[B_MAX_BUCKETS];  // bucket b holds m <= bucket_max_n[b]
-  int ns[B_MAX_BUCKETS];
-  int nw[B_MAX_BUCKETS];
-  int nw_max;                       // largest window in the table (smem sizing)
-};
-
-struct BatchedDesc {
-  double* H;
-  double* Z;
-  double* wr;
-  double* wi;
-  long long ldh, ldz;
-  int n;
-  int pad;
-};
-
-struct BatchedScratch {   // per thread block, global memory
-  double* V;        // nw_max^2
-  double* vbuf;     // 4 nw_max
-  double* cand_re;  // nw_max
-  double* cand_im;
-  double* pairs;    // 2 * (MAX_BULGES_PER_CHAIN + 4)
-};
+#include "batched.cuh"
 
 struct BShared {
   double v1[MAX_BULGES_PER_CHAIN], v2[MAX_BULGES_PER_CHAIN], tau[MAX_BULGES_PER_CHAIN];

@@ -33,6 +33,7 @@ const char* status_string(int code) {
     case SCHUR_ERR_NOMEM: return "device memory allocation failed";
     case SCHUR_ERR_WORKSPACE: return "workspace too small";
     case SCHUR_ERR_UNSUPPORTED: return "unsupported argument combination";
+    case SCHUR_ERR_TOO_LARGE: return "order above the fixed limit (1024) of the no-allocation entry point";
     default: break;
   }
   if (code < 0) return "invalid argument";
