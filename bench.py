@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=2023)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the batched (4096 x n in [32,768]) and backward (256 x n in [64,1024]) metrics")
     return ap.parse_args()
 
 
@@ -139,6 +141,85 @@ def reference_arm(args):
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def secondary_metrics(api, inputs, torch, np):
+    """The other two metrics of the workload list, each next to the plain
+    single-matrix path on the same GPU:
+      batched:  4096 hess_n matrices, n uniform in [32, 768] (seed 2024), one
+                persistent graph-captured launch -> matrices/s;
+      backward: 256 hess_n matrices, n uniform in [64, 1024] (seed 2025), loss
+                sum |lambda|^2 -> batched backward time / batched forward time."""
+
+    def load(sizes, seed):
+        Hs = []
+        for b, n in enumerate(sizes):
+            H = inputs.hessrand(int(n), [seed, b])
+            Hs.append(torch.from_numpy(np.ascontiguousarray(H.T)).cuda().t())
+        return Hs
+
+    def buffers(Hs):
+        Ss = [h.clone() for h in Hs]
+        Zs = [api.new_colmajor(h.shape[0]) for h in Hs]
+        wr = [torch.empty(h.shape[0], dtype=torch.float64, device="cuda") for h in Hs]
+        wi = [torch.empty_like(w) for w in wr]
+        return Ss, Zs, wr, wi
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, out
+
+    out = {}
+    sizes = inputs.batch_sizes(4096, 32, 768, 2024)
+    Hs = load(sizes, 2024)
+    bufs = buffers(Hs)
+    api.schur_batched_inplace(*bufs)                     # warm-up
+    for s_, h in zip(bufs[0], Hs):
+        s_.copy_(h)
+    t, info = timed(lambda: api.schur_batched_inplace(*bufs))
+    single = []
+    for h in Hs[:16]:
+        S1, Z1 = h.clone(), api.new_colmajor(h.shape[0])
+        w1 = torch.empty(h.shape[0], dtype=torch.float64, device="cuda")
+        w2 = torch.empty_like(w1)
+        o = api._lib.make_opts(torch.cuda.current_stream().cuda_stream)
+        ts, _ = timed(lambda: api.schur_inplace(S1, Z1, w1, w2, o))
+        single.append(ts)
+    out["batched"] = {"workload": "4096 hess_n, n uniform in [32,768], seed 2024", "mats_per_s": 4096 / t,
+                      "seconds": t, "failed": int(sum(1 for i in info if i)), "launches": 2,
+                      "single_path_mats_per_s": len(single) / sum(single),
+                      "single_path_sample": "first 16 matrices of the batch, one schur_hessenberg call each"}
+    del Hs, bufs
+    torch.cuda.empty_cache()
+    sizes = inputs.batch_sizes(256, 64, 1024, 2025)
+    Hs = load(sizes, 2025)
+    bufs = buffers(Hs)
+    api.schur_batched_inplace(*bufs)                     # warm-up
+    for s_, h in zip(bufs[0], Hs):
+        s_.copy_(h)
+    tf, info = timed(lambda: api.schur_batched_inplace(*bufs))
+    Ss, Zs, wr, wi = bufs
+    gr = [2 * a for a in wr]
+    gi = [2 * b for b in wi]
+    api.eig_backward_batched(Ss, Zs, wr, wi, gr, gi)     # warm-up
+    tb, _ = timed(lambda: api.eig_backward_batched(Ss, Zs, wr, wi, gr, gi))
+    one_f, one_b = 0.0, 0.0
+    for h in Hs[:8]:
+        ts, (S1, Z1, a, b, rc) = timed(lambda: api.schur(h))
+        tg, _ = timed(lambda: api.eig_backward(S1, Z1, a, b, 2 * a, 2 * b))
+        one_f += ts
+        one_b += tg
+    out["backward"] = {"workload": "256 hess_n, n uniform in [64,1024], seed 2025, L = sum |lambda|^2",
+                       "forward_s": tf, "backward_s": tb, "backward_over_forward": tb / tf,
+                       "failed": int(sum(1 for i in info if i)),
+                       "single_path_backward_over_forward": one_b / one_f,
+                       "single_path_sample": "first 8 matrices, schur_hessenberg + schur_eig_backward each"}
+    return out
 
 
 def main():
@@ -269,6 +350,8 @@ def main():
     dgemm_tflops = 3 * 2 * 8192 ** 3 / (g0.elapsed_time(g1) / 1e3) / 1e12
     del a, b
 
+    sec = None if args.no_secondary else secondary_metrics(api, inputs, torch, np)
+
     st = stats[-1]
     upd_flops = sum(s["sweep_gemm_flops"] for s in stats)
     upd_ms = sum(s["t_update_ms"] for s in stats)
@@ -317,6 +400,7 @@ def main():
         "iterations": {"aed": st["aed_steps"], "sweeps": st["sweeps"], "deflated_by_aed": st["deflated_by_aed"]},
         "flops": {"reflector_algorithmic": st["reflector_flops"], "sweep_gemm_executed": st["sweep_gemm_flops"],
                   "aed_gemm_executed": st["aed_gemm_flops"]},
+        "secondary": sec,
         "check": {"residual_probe": resid, "orthogonality_probe": orth, "trace_rel_err": trace_err},
         "context": "paper Table 4: syn_20000 StarNEig 68 s on 25 Skylake cores (different matrix family)",
     }

@@ -345,18 +345,20 @@ __global__ void k_batched_prep_z(const BatchedDesc* desc, int batch, int zinit) 
 // ===========================================================================
 namespace schur {
 
-// Default per-bucket table (same rule as the single-matrix table, windows
-// capped for the shared-memory window of the batched engine).
+// Default per-bucket table: the autotuner's choice (tune.autotune_batched on
+// GB300, 608 hess_n matrices with n uniform in [32, 768]; timings in the
+// profiles folder).  Windows are capped for the batched engine's shared-memory
+// window.
 static void default_batched_params(BatchedParams& P) {
   memset(&P, 0, sizeof(P));
   P.nmin = 75;
   P.nibble = 14;
   P.exc_period = 6;
-  P.nbuckets = 3;
-  int mx[3] = {149, 589, 1 << 30};
-  int ns[3] = {8, 8, 32};
-  int nw[3] = {24, 32, 64};
-  for (int b = 0; b < 3; ++b) {
+  P.nbuckets = 4;
+  int mx[4] = {149, 299, 589, 1 << 30};
+  int ns[4] = {4, 8, 32, 16};
+  int nw[4] = {16, 24, 64, 48};
+  for (int b = 0; b < 4; ++b) {
     P.bucket_max_n[b] = mx[b];
     P.ns[b] = ns[b];
     P.nw[b] = nw[b];
