@@ -102,6 +102,7 @@ typedef struct {
   double aed_cycles_schur;
   double aed_cycles_post;
   long long kernel_launches; /* kernels launched by the call (all levels) */
+  double t_z_ms;            /* products applied to Z on the second stream (overlaps the rest) */
 } schur_stats;
 
 /* Fill *opts with the defaults listed above. Returns SCHUR_OK. */

@@ -68,6 +68,7 @@ class SchurStats(ctypes.Structure):
         ("aed_cycles_schur", c_double),
         ("aed_cycles_post", c_double),
         ("kernel_launches", ctypes.c_longlong),
+        ("t_z_ms", c_double),
     ]
 
 

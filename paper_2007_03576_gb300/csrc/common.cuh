@@ -75,6 +75,7 @@ struct UpdTask {
   int tile0;   // first tile index of this task in the launch
   int ntile;
   const int* gate;  // optional: skip when *gate == 0 (e.g. AED deflated nothing)
+  int lbw, ubw;     // U[k, i] = 0 when k - i > lbw or i - k > ubw (L = dense)
 };
 
 struct UpdArgs {

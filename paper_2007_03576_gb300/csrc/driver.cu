@@ -61,11 +61,13 @@ struct LevelSizes {
   int n;       // order of the matrix at this level
   int nwmax;   // largest AED window
   int nsmax;   // most shifts
+  size_t arena;  // level 0: doubles of the arena behind the Z stream
   size_t bytes() const {
     size_t b = 0;
     b += align_up(sizeof(Ctl));
     b += align_up((size_t)MAX_CHAINS * KWIN_MAX * KWIN_MAX * sizeof(double));  // chase U
     b += align_up((size_t)nwmax * nwmax * sizeof(double));                       // V
+    b += align_up(arena * sizeof(double));
     b += (nwmax > NW_SMEM_MAX) ? align_up((size_t)nwmax * nwmax * sizeof(double)) : 0;  // T
     b += 2 * align_up((size_t)std::max(nwmax, 4) * sizeof(double));              // candidates
     b += align_up((size_t)(nsmax + 8) * sizeof(double));                         // pairs
@@ -86,7 +88,20 @@ static void level_plan(int n, const schur_opts& o, std::vector<LevelSizes>& out)
       if (o.aed_window > 0) nw = o.aed_window;
     }
     nw = std::min(std::min(nw, m), 1024);
-    LevelSizes L{m, nw, ns};
+    size_t arena = 0;
+    if (lev == 0) {
+      // one sweep's window transforms plus an AED's V: chains x steps x kwin^2
+      int nbc = o.bulges_per_chain > 0 ? o.bulges_per_chain : 16;
+      nbc = std::max(1, std::min(nbc, MAX_BULGES_PER_CHAIN));
+      int kwin = std::min(KWIN_MAX, std::max(6 * nbc, 48));
+      int delta = std::max(1, kwin - 3 * nbc - 1);
+      size_t nchain = (size_t)std::max(1, (ns / 2 + nbc - 1) / nbc);
+      size_t steps = (size_t)m / delta + 3 * nchain * ((size_t)(2 * kwin + 4 * nbc) / delta + 2) + 8;
+      arena = (nchain * steps + 2) * (size_t)kwin * kwin + 2 * (size_t)nw * nw;
+      arena = std::min(arena, (size_t)(1ull << 27));                       // at most 1 GiB
+      arena = std::max(arena, (size_t)MAX_CHAINS * KWIN_MAX * KWIN_MAX + (size_t)nw * nw);
+    }
+    LevelSizes L{m, nw, ns, arena};
     out.push_back(L);
     if (nw <= NW_SMEM_MAX) break;
     m = nw;
@@ -120,6 +135,11 @@ void Solver::carve(char* base, int n) {
     v.ctl = (Ctl*)take(sizeof(Ctl));
     v.ubuf = (double*)take((size_t)MAX_CHAINS * KWIN_MAX * KWIN_MAX * sizeof(double));
     v.V = (double*)take((size_t)L.nwmax * L.nwmax * sizeof(double));
+    if (L.arena) {
+      arena = (double*)take(L.arena * sizeof(double));
+      arena_cap = L.arena;
+      arena_cur = 0;
+    }
     v.T = (L.nwmax > NW_SMEM_MAX) ? (double*)take((size_t)L.nwmax * L.nwmax * sizeof(double)) : nullptr;
     v.cand_re = (double*)take((size_t)std::max(L.nwmax, 4) * sizeof(double));
     v.cand_im = (double*)take((size_t)std::max(L.nwmax, 4) * sizeof(double));
@@ -179,6 +199,25 @@ void PhaseTimer::flush() {
   used = 0;
 }
 
+void PhaseTimer::flush_completed() {
+  size_t i = 0;
+  for (; i < used; ++i) {
+    if (cudaEventQuery(pool[2 * i + 1]) != cudaSuccess) break;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) ms[phase_of[i]] += t;
+  }
+  cudaGetLastError();
+  if (i == 0) return;
+  // keep the unfinished pairs at the front (swap events and phases)
+  size_t k = 0;
+  for (size_t j = i; j < used; ++j, ++k) {
+    std::swap(pool[2 * k], pool[2 * j]);
+    std::swap(pool[2 * k + 1], pool[2 * j + 1]);
+    phase_of[k] = phase_of[j];
+  }
+  used = k;
+}
+
 PhaseTimer::~PhaseTimer() {
   for (auto e : pool) cudaEventDestroy(e);
 }
@@ -214,8 +253,102 @@ Solver::Solver(const schur_opts* o) {
 }
 
 Solver::~Solver() {
+  if (zst) {
+    cudaStreamSynchronize(zst);
+    cudaStreamDestroy(zst);
+  }
+  for (auto& r : live)
+    if (r.ev) cudaEventDestroy(r.ev);
+  for (auto& e : spare_events) cudaEventDestroy(e);
+  if (ev_ready) cudaEventDestroy(ev_ready);
+  if (ev_zdone) cudaEventDestroy(ev_zdone);
   if (hctl) cudaFreeHost(hctl);
   if (owned) cudaFree(owned);
+}
+
+// Second stream for Z (level 0).  Lowest priority so that the critical path
+// (chase, AED, H updates) gets the SMs first.
+void Solver::init_zstream() {
+  int lo = 0, hi = 0;
+  ck(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  ck(cudaStreamCreateWithPriority(&zst, cudaStreamNonBlocking, lo));
+  ck(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
+  ck(cudaEventCreateWithFlags(&ev_zdone, cudaEventDisableTiming));
+  ztimer.on = timer.on;
+}
+
+// Regions of the arena are handed out in order, wrapping at the end; a new
+// region waits (on the main stream) for every older live region up to the
+// last one it overlaps.
+double* Solver::arena_alloc(size_t n) {
+  size_t a = (arena_cur + n > arena_cap) ? 0 : arena_cur;
+  size_t b = a + n;
+  // a region still held by deferred Z products is handed to zst first
+  for (const PendingZ& p : zpending)
+    if (p.a < b && a < p.b) {
+      z_flush();
+      break;
+    }
+  int last = -1;
+  for (size_t i = 0; i < live.size(); ++i)
+    if (live[i].a < b && a < live[i].b) last = (int)i;
+  for (int i = 0; i <= last; ++i) {
+    Region r = live.front();
+    live.pop_front();
+    if (r.ev) {
+      ck(cudaStreamWaitEvent(st, r.ev, 0));
+      spare_events.push_back(r.ev);
+    }
+  }
+  arena_cur = b;
+  return arena + a;
+}
+
+void Solver::arena_release(double* p, size_t n, bool z_reader) {
+  Region r{(size_t)(p - arena), (size_t)(p - arena) + n, nullptr};
+  if (z_reader) {
+    if (spare_events.empty()) {
+      cudaEvent_t e;
+      ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      spare_events.push_back(e);
+    }
+    r.ev = spare_events.back();
+    spare_events.pop_back();
+    ck(cudaEventRecord(r.ev, zst));
+  }
+  live.push_back(r);
+}
+
+void Solver::z_defer(std::vector<UpdTask>& tasks, const double* p, size_t n) {
+  zpending.push_back(PendingZ{std::move(tasks), (size_t)(p - arena), (size_t)(p - arena) + n});
+}
+
+// The deferred tasks go to zst in the order they were deferred (Z's columns
+// overlap between chase steps); their arena regions become live, each behind
+// the event recorded after the last of them.
+void Solver::z_flush() {
+  if (zpending.empty()) return;
+  std::vector<PendingZ> pend;
+  pend.swap(zpending);
+  ck(cudaEventRecord(ev_ready, st));
+  ck(cudaStreamWaitEvent(zst, ev_ready, 0));
+  for (PendingZ& p : pend) run_updates(p.tasks, zst, true);
+  for (PendingZ& p : pend) arena_release(arena + p.a, p.b - p.a, true);
+}
+
+void Solver::z_async(std::vector<UpdTask>& tasks, cudaEvent_t done) {
+  z_flush();
+  ck(cudaEventRecord(ev_ready, st));
+  ck(cudaStreamWaitEvent(zst, ev_ready, 0));
+  run_updates(tasks, zst, true);
+  if (done) ck(cudaEventRecord(done, zst));
+}
+
+void Solver::drain_z() {
+  if (!zst) return;
+  z_flush();
+  ck(cudaEventRecord(ev_zdone, zst));
+  ck(cudaStreamWaitEvent(st, ev_zdone, 0));
 }
 
 int Solver::setup(int n) {
@@ -242,6 +375,7 @@ void Solver::read_ctl(const Ctl* dctl) {
   ck(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   ck(cudaStreamSynchronize(st));
   timer.flush();
+  if (zst) ztimer.flush_completed();
 }
 
 DeflParams Solver::defl(int n) const {
@@ -255,7 +389,10 @@ DeflParams Solver::defl(int n) const {
 
 // Issue a list of off-window products (split in launches of at most
 // MAX_UPD_TASKS tasks; tasks within a launch must not overlap).
-void Solver::run_updates(std::vector<UpdTask>& tasks) {
+void Solver::run_updates(std::vector<UpdTask>& tasks, cudaStream_t sarg, bool on_z) {
+  cudaStream_t s = on_z ? sarg : st;
+  PhaseTimer& tm = on_z ? ztimer : timer;
+  const int phase = on_z ? PH_Z : cur_update_phase;
   size_t i = 0;
   while (i < tasks.size()) {
     UpdArgs a;
@@ -272,20 +409,32 @@ void Solver::run_updates(std::vector<UpdTask>& tasks) {
     int tn = apply_u_tn(maxL);
     a.tn = tn;
     int tile = 0;
+    const int RG = CTA_THREADS / (tn / 4);  // output rows per row block of k_apply_u
     for (int t = 0; t < cnt; ++t) {
       a.t[t].tile0 = tile;
       a.t[t].ntile = (a.t[t].nvec + tn - 1) / tn;
       tile += a.t[t].ntile;
-      double f = 2.0 * a.t[t].L * (double)a.t[t].L * a.t[t].nvec;
-      if (cur_flops) *cur_flops += f;
+      // flops the kernel executes: (row block, 16 k) tiles outside the band
+      // are skipped exactly as in k_apply_u
+      const UpdTask& q = a.t[t];
+      double entries = 0.0;
+      for (int r0 = 0; r0 < q.L; r0 += RG)
+        for (int k0 = 0; k0 < q.L; k0 += 16) {
+          int r1 = std::min(q.L, r0 + RG) - 1, k1 = std::min(q.L, k0 + 16) - 1;
+          bool skip = (k0 - (r0 + RG - 1) > q.lbw) || (r0 - k1 > q.ubw);
+          if (!skip) entries += (double)(r1 - r0 + 1) * (k1 - k0 + 1);
+        }
+      if (cur_flops) *cur_flops += 2.0 * entries * q.nvec;
     }
     size_t smem = apply_u_smem_bytes(tn, maxL);
-    int per_sm = std::max(1, (int)((226 * 1024) / std::max<size_t>(smem, 1)));
-    int grid = std::min(tile, num_sms() * std::min(per_sm, 8));
-    int tok = timer.begin(st, cur_update_phase);
+    // one tile per block: blocks stay short (~0.3 ms), so that when the two
+    // streams compete the block scheduler can hand freed SMs to the
+    // high-priority stream (H updates, chase, AED) between tiles
+    int grid = std::min(tile, 1 << 20);
+    int tok = tm.begin(s, phase);
     ++g_stats.kernel_launches;
-    ck(launch_apply_u(tn, grid, smem, st, a));
-    timer.end(st, tok);
+    ck(launch_apply_u(tn, grid, smem, s, a));
+    tm.end(s, tok);
     if (cur_update_phase == PH_UPDATE && timer.depth == 0 && count_launches) g_stats.update_launches += 1;
   }
 }
@@ -304,16 +453,33 @@ static UpdTask make_task(double* A, long long lda, int side, int r0, int c0, int
   t.U = U;
   t.ldu = ldu;
   t.gate = gate;
+  t.lbw = L;
+  t.ubw = L;
   return t;
+}
+
+// Band of the accumulated transform U of one chase window (U = product of the
+// window's reflectors in order; U[r, c] can be nonzero only if column c is
+// reached from row r by overlapping reflectors applied later):
+//  - downward an index only follows the bulge that first covers it (the bulge
+//    ahead is three rows lower and is moved first in every step), so
+//    c - r <= (steps in the window - 1) + 2 <= delta + 1;
+//  - upward it passes to the next bulge above once per step, two rows each
+//    time, so r - c <= 2 + 2 min(nb - 1, delta - 1).
+// Entries outside the band are exact zeros of the identity U starts from.
+static void set_chase_band(UpdTask& t, int nb, int delta) {
+  t.lbw = std::min(t.L, 2 + 2 * std::min(nb - 1, delta - 1));
+  t.ubw = std::min(t.L, delta + 1);
 }
 
 // Apply an accumulated L x L transform of the diagonal block [k0, k0+L) to
 // the rest of H (full Schur form: columns right of the block, rows above it)
 // and to Z's columns k0..k0+L-1.
-void Solver::apply_block_transform(const Mat3& M, int k0, int L, const double* U, int ldu, const int* gate) {
+void Solver::apply_block_transform(const Mat3& M, int k0, int L, const double* U, int ldu, const int* gate,
+                                   bool with_z) {
   std::vector<UpdTask> t1, t2;
   if (k0 + L < M.n) t1.push_back(make_task(M.H, M.ldh, 0, k0, k0 + L, L, M.n - k0 - L, U, ldu, gate));
-  if (M.Z) t1.push_back(make_task(M.Z, M.ldz, 1, 0, k0, L, M.zrows, U, ldu, gate));
+  if (M.Z && with_z) t1.push_back(make_task(M.Z, M.ldz, 1, 0, k0, L, M.zrows, U, ldu, gate));
   if (k0 > 0) t2.push_back(make_task(M.H, M.ldh, 1, 0, k0, L, k0, U, ldu, gate));
   // left products and right products touch H[k0.., k0..] on disjoint sets:
   // left: rows k0..k0+L-1, columns >= k0+L; right: rows < k0, columns of
@@ -350,6 +516,7 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
     last = std::max(last, start[c] + nl);
   }
   size_t smem = chase_smem_bytes(kwin);
+  const bool zasync = (lev == 0 && zst != nullptr && M.Z != nullptr);
   for (int s = 0; s < last; ++s) {
     ChaseArgs a;
     memset(&a, 0, sizeof(a));
@@ -380,26 +547,42 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
     }
     if (na == 0) continue;
     a.nchain = na;
+    // this step's window transforms: from the arena while the Z stream may
+    // still need them, else the level's buffer
+    const size_t need = (size_t)na * kwin * kwin;
+    double* ubase = zasync ? arena_alloc(need) : Lv.ubuf;
     int tok = timer.begin(st, PH_CHASE);
     ++g_stats.kernel_launches;
-    k_chase<<<na, CTA_THREADS, smem, st>>>(M.H, M.ldh, dpairs, Lv.ubuf, a);
+    k_chase<<<na, CTA_THREADS, smem, st>>>(M.H, M.ldh, dpairs, ubase, a);
     ck(cudaGetLastError());
     timer.end(st, tok);
     g_stats.window_launches += 1;
     if (lev == 0) g_stats.chase_launches += 1;
     count_launches = (lev == 0);
-    std::vector<UpdTask> t1, t2;
+    std::vector<UpdTask> t1, t2, tz;
     for (int i = 0; i < na; ++i) {
       const ChainDesc& d = a.c[i];
       int L = d.we - d.ws + 1;
-      const double* U = Lv.ubuf + d.uoff;
-      if (d.we + 1 < M.n) t1.push_back(make_task(M.H, M.ldh, 0, d.ws, d.we + 1, L, M.n - d.we - 1, U, kwin, nullptr));
-      if (M.Z) t1.push_back(make_task(M.Z, M.ldz, 1, 0, d.ws, L, M.zrows, U, kwin, nullptr));
-      if (d.ws > 0) t2.push_back(make_task(M.H, M.ldh, 1, 0, d.ws, L, d.ws, U, kwin, nullptr));
+      const double* U = ubase + d.uoff;
+      if (d.we + 1 < M.n) {
+        t1.push_back(make_task(M.H, M.ldh, 0, d.ws, d.we + 1, L, M.n - d.we - 1, U, kwin, nullptr));
+        set_chase_band(t1.back(), d.nb, delta);
+      }
+      if (M.Z) {
+        std::vector<UpdTask>& tzv = zasync ? tz : t1;
+        tzv.push_back(make_task(M.Z, M.ldz, 1, 0, d.ws, L, M.zrows, U, kwin, nullptr));
+        set_chase_band(tzv.back(), d.nb, delta);
+      }
+      if (d.ws > 0) {
+        t2.push_back(make_task(M.H, M.ldh, 1, 0, d.ws, L, d.ws, U, kwin, nullptr));
+        set_chase_band(t2.back(), d.nb, delta);
+      }
     }
+    if (zasync) z_defer(tz, ubase, need);   // issued on zst at the end of the sweep
     run_updates(t1);
     run_updates(t2);
   }
+  if (zasync) z_flush();
   if (lev == 0) {
     // algorithmic flops of applying the reflectors directly (12 flops per
     // row/column entry of each 3x3 reflector): every bulge passes rows
@@ -434,6 +617,7 @@ int Solver::qr_block(const Mat3& M, int lev, int ilo, int ihi) {
       continue;
     }
     if (m == 2) {
+      if (lev == 0) drain_z();
       ++g_stats.kernel_launches;
       k_std2<<<1, CTA_THREADS, 0, st>>>(M.H, M.ldh, M.n, M.Z, M.ldz, M.Z ? M.zrows : 0, ktop);
       ck(cudaGetLastError());
@@ -442,6 +626,7 @@ int Solver::qr_block(const Mat3& M, int lev, int ilo, int ihi) {
       continue;
     }
     if (m <= opts.nmin) {
+      if (lev == 0) drain_z();
       size_t smem = (size_t)(m | 1) * m * sizeof(double);
       int tok = timer.begin(st, PH_SMALL);
       ++g_stats.kernel_launches;
@@ -492,37 +677,47 @@ int Solver::aed(const Mat3& M, int lev, int ktop, int kbot, int nw, int ns_max, 
   int kwtop = kbot - nw + 1;
   double* saved = cur_flops;
   if (lev == 0) cur_flops = &g_stats.aed_gemm_flops;
+  // ring slot of V (reused only after the Z stream has applied it)
+  const bool zasync = (lev == 0 && zst != nullptr && M.Z != nullptr);
+  double* V = zasync ? arena_alloc((size_t)nw * nw) : Lv.V;
   int tok = timer.begin(st, PH_AED);
   if (nw <= NW_SMEM_MAX) {
     size_t smem = (size_t)(nw | 1) * nw * sizeof(double);
     ++g_stats.kernel_launches;
-    k_aed_small<<<1, CTA_THREADS, smem, st>>>(M.H, M.ldh, ktop, kbot, nw, Lv.V, nw, Lv.cand_re, Lv.cand_im, Lv.vbuf,
+    k_aed_small<<<1, CTA_THREADS, smem, st>>>(M.H, M.ldh, ktop, kbot, nw, V, nw, Lv.cand_re, Lv.cand_im, Lv.vbuf,
                                              dp, dpw, Lv.ctl);
     ck(cudaGetLastError());
   } else {
     ++g_stats.kernel_launches;
-    k_copy_window<<<std::min(nw, 4 * num_sms()), CTA_THREADS, 0, st>>>(M.H, M.ldh, kwtop, nw, Lv.T, nw, Lv.V, nw);
+    k_copy_window<<<std::min(nw, 4 * num_sms()), CTA_THREADS, 0, st>>>(M.H, M.ldh, kwtop, nw, Lv.T, nw, V, nw);
     ck(cudaGetLastError());
-    Mat3 W{Lv.T, nw, nw, Lv.V, nw, nw};
+    Mat3 W{Lv.T, nw, nw, V, nw, nw};
     double* keep = cur_flops;
     cur_flops = nullptr;
     int inner = qr_block(W, lev + 1, 0, nw - 1);
     cur_flops = keep;
     ++g_stats.kernel_launches;
-    k_aed_big_post<<<1, CTA_THREADS, 0, st>>>(M.H, M.ldh, ktop, kbot, nw, Lv.T, nw, Lv.V, nw, Lv.cand_re, Lv.cand_im,
+    k_aed_big_post<<<1, CTA_THREADS, 0, st>>>(M.H, M.ldh, ktop, kbot, nw, Lv.T, nw, V, nw, Lv.cand_re, Lv.cand_im,
                                               Lv.vbuf, dp, Lv.ctl, inner);
     ck(cudaGetLastError());
   }
   timer.end(st, tok);
   int saved_phase = cur_update_phase;
   cur_update_phase = PH_AED_UPDATE;
-  apply_block_transform(M, kwtop, nw, Lv.V, nw, &Lv.ctl->nd);
-  cur_update_phase = saved_phase;
+  apply_block_transform(M, kwtop, nw, V, nw, &Lv.ctl->nd, !zasync);
   ++g_stats.kernel_launches;
   k_make_pairs<<<1, 32, 0, st>>>(M.H, M.ldh, ktop, kbot, std::min(ns_max, Lv.nsmax + 8 - 4), ndfl, 6, Lv.cand_re,
                                  Lv.cand_im, Lv.pairs, Lv.ctl);
   ck(cudaGetLastError());
   read_ctl(Lv.ctl);
+  if (zasync) {
+    if (hctl->nd > 0) {
+      std::vector<UpdTask> tz{make_task(M.Z, M.ldz, 1, 0, kwtop, nw, M.zrows, V, nw, nullptr)};
+      z_async(tz, nullptr);
+    }
+    arena_release(V, (size_t)nw * nw, hctl->nd > 0);
+  }
+  cur_update_phase = saved_phase;
   cur_flops = saved;
   return hctl->nd;
 }
@@ -600,13 +795,20 @@ extern "C" int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, d
     }
     Mat3 M{H, ldh, n, Z, ldz, n};
     s.cur_flops = &g_stats.sweep_gemm_flops;
+    if (Z) s.init_zstream();
     int info = s.qr_block(M, 0, 0, n - 1);
+    s.drain_z();
     ++g_stats.kernel_launches;
     k_extract_eigs<<<std::max(1, std::min((n + 255) / 256, 4 * num_sms())), 256, 0, s.st>>>(H, ldh, n, wr, wi);
     ck(cudaGetLastError());
     ck(cudaStreamSynchronize(s.st));
     s.timer.flush();
     s.read_ctl(s.levels[0].ctl);
+    if (s.zst) {
+      ck(cudaStreamSynchronize(s.zst));
+      s.ztimer.flush_completed();
+      for (int ph = 0; ph < PH_COUNT; ++ph) s.timer.ms[ph] += s.ztimer.ms[ph];
+    }
     g_stats.aed_cycles_schur = (double)s.hctl->cyc_schur;
     g_stats.aed_cycles_post = (double)s.hctl->cyc_defl;
     g_stats.t_chase_ms = s.timer.ms[PH_CHASE];
@@ -614,6 +816,7 @@ extern "C" int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, d
     g_stats.t_aed_ms = s.timer.ms[PH_AED];
     g_stats.t_aed_update_ms = s.timer.ms[PH_AED_UPDATE];
     g_stats.t_small_ms = s.timer.ms[PH_SMALL];
+    g_stats.t_z_ms = s.timer.ms[PH_Z];
     return info;
   } catch (const CudaError&) {
     return SCHUR_ERR_CUDA;

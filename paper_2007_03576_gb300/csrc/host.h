@@ -8,7 +8,9 @@
 #include "../../include/schur_gb300.h"
 #include "common.cuh"
 
-#define KWIN_MAX 128   // largest bulge-chase window
+#define KWIN_MAX 112   // largest bulge-chase window (window + U in shared memory: 2 (k+1) k doubles)
+
+#include <deque>
 
 namespace schur {
 
@@ -43,7 +45,7 @@ struct Level {
 };
 
 // Per-phase device timing with CUDA events (opts.timing = 1).
-enum Phase { PH_CHASE = 0, PH_UPDATE = 1, PH_AED = 2, PH_AED_UPDATE = 3, PH_SMALL = 4, PH_COUNT = 5 };
+enum Phase { PH_CHASE = 0, PH_UPDATE = 1, PH_AED = 2, PH_AED_UPDATE = 3, PH_SMALL = 4, PH_Z = 5, PH_COUNT = 6 };
 
 struct PhaseTimer {
   bool on = false;
@@ -51,10 +53,11 @@ struct PhaseTimer {
   std::vector<int> phase_of;   // phase of event pair i
   size_t used = 0;             // event pairs recorded since the last flush
   int depth = 0;               // > 0 while inside a timed region (nested launches not timed)
-  double ms[PH_COUNT] = {0, 0, 0, 0, 0};
+  double ms[PH_COUNT] = {0, 0, 0, 0, 0, 0};
   int begin(cudaStream_t st, int phase);
   void end(cudaStream_t st, int token);
   void flush();                // after a stream synchronisation
+  void flush_completed();      // pairs whose end event has completed (other stream)
   ~PhaseTimer();
 };
 
@@ -69,6 +72,34 @@ struct Solver {
   int cur_update_phase = PH_UPDATE;
   bool count_launches = false;
   PhaseTimer timer;
+  // Z is only ever multiplied from the right and nothing on H's side reads
+  // it, so at level 0 its updates run on a second, low-priority stream (zst)
+  // behind events; the chase / AED transforms they read sit in an arena whose
+  // regions are reused only after zst has consumed them.  A sweep's Z
+  // products are held back (zpending) until the sweep's H updates have been
+  // issued, so that they fill the SMs that the next (one-block) AED leaves idle
+  // instead of competing with the sweep's own H updates.
+  cudaStream_t zst = nullptr;
+  PhaseTimer ztimer;
+  cudaEvent_t ev_ready = nullptr, ev_zdone = nullptr;
+  // Circular arena (level 0) holding the chase U's and AED V's that the Z
+  // stream has not consumed yet; a region is reused only after the event
+  // recorded behind its last Z-stream reader.
+  struct Region {
+    size_t a, b;           // [a, b) in doubles
+    cudaEvent_t ev;        // nullptr: only main-stream readers
+  };
+  double* arena = nullptr;
+  size_t arena_cap = 0, arena_cur = 0;
+  std::deque<Region> live;
+  struct PendingZ {
+    std::vector<UpdTask> tasks;
+    size_t a, b;           // arena region the tasks read
+  };
+  std::vector<PendingZ> zpending;
+  std::vector<cudaEvent_t> spare_events;
+  double* arena_alloc(size_t n);                 // waits (on st) for overlapping live regions
+  void arena_release(double* p, size_t n, bool z_reader);  // after the readers were issued
   std::vector<Level> levels;
 
   explicit Solver(const schur_opts* o);
@@ -77,8 +108,14 @@ struct Solver {
   void carve(char* base, int n);
   void read_ctl(const Ctl* d);
   DeflParams defl(int n) const;
-  void run_updates(std::vector<UpdTask>& tasks);
-  void apply_block_transform(const Mat3& M, int k0, int L, const double* U, int ldu, const int* gate);
+  void run_updates(std::vector<UpdTask>& tasks, cudaStream_t s = nullptr, bool on_z = false);
+  void apply_block_transform(const Mat3& M, int k0, int L, const double* U, int ldu, const int* gate,
+                             bool with_z = true);
+  void z_async(std::vector<UpdTask>& tasks, cudaEvent_t done);   // Z tasks on zst after st's current point
+  void z_defer(std::vector<UpdTask>& tasks, const double* p, size_t n);  // held until z_flush
+  void z_flush();                                                // issue zpending on zst after st's current point
+  void drain_z();                                                // st waits for all of zst's work
+  void init_zstream();
   void sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs, int npairs, int nbc_req);
   int qr_block(const Mat3& M, int lev, int ilo, int ihi);
   int aed(const Mat3& M, int lev, int ktop, int kbot, int nw, int ns_max, int ndfl);

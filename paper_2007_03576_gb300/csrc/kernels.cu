@@ -402,19 +402,26 @@ __global__ void __launch_bounds__(CTA_THREADS) k_apply_u(const __grid_constant__
         sU[kk * LDU + i] = t.U[(kc + kk) + (long long)i * t.ldu];
       }
       __syncthreads();
-      for (int kk = 0; kk < kn; ++kk) {
-        const double* xr = sX + (size_t)(kc + kk) * LDV + vg * CN;
-        double xv[CN];
-#pragma unroll
-        for (int c = 0; c < CN; ++c) xv[c] = xr[c];
-        const double* ur = sU + (size_t)kk * LDU;
+      // k in blocks of 16; a block of output rows (rows RG*a .. RG*a+RG-1) is
+      // skipped where U[k, i] is structurally zero for all its rows:
+      // k - i > lbw or i - k > ubw (banded window transforms of the chase)
+      for (int k16 = 0; k16 < kn; k16 += 16) {
+        const int kg0 = kc + k16;
+        const int kend = min(kn, k16 + 16);
+        const int kg1 = kc + kend - 1;
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
           if (a < RM) {
-            int i = rg + RG * a;
-            double u = (i < L) ? ur[i] : 0.0;
+            const bool skip = (kg0 - (RG * a + RG - 1) > t.lbw) || (RG * a - kg1 > t.ubw);
+            if (!skip) {
+              const int i = rg + RG * a;
+              for (int kk = k16; kk < kend; ++kk) {
+                const double* xr = sX + (size_t)(kc + kk) * LDV + vg * CN;
+                double u = (i < L) ? sU[(size_t)kk * LDU + i] : 0.0;
 #pragma unroll
-            for (int c = 0; c < CN; ++c) acc[a][c] = fma(u, xv[c], acc[a][c]);
+                for (int c = 0; c < CN; ++c) acc[a][c] = fma(u, xr[c], acc[a][c]);
+              }
+            }
           }
         }
       }

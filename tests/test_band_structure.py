@@ -1,0 +1,68 @@
+"""Host-side check of the band of the chase windows' accumulated transforms.
+
+k_apply_u skips (16 x row-block) tiles of U that are structurally zero.  The
+driver declares, for a window of a chain of nb bulges moved delta steps, the
+band  r - c <= 2 + 2 min(nb - 1, delta - 1)  and  c - r <= delta + 1.  This
+test re-derives the window schedule of a sweep (Sec. 2.3/2.4: chains of
+bulges, chain c started S launches after chain c - 1, each launch moving every
+chain delta steps) and propagates the nonzero pattern of U through the
+window's reflectors (a reflector on rows/columns k..k+2 couples them), for
+several chain sizes, including the first (bulge introduction) and last
+(bulges leaving) windows."""
+
+import numpy as np
+import pytest
+
+KWIN_MAX, MAX_CHAINS, MAX_BULGES = 112, 32, 32
+
+
+def schedule(lo, hi, npairs, nbc_req):
+    nbc = max(1, min(nbc_req, npairs, MAX_BULGES))
+    nbc = max(nbc, (npairs + MAX_CHAINS - 1) // MAX_CHAINS)
+    kwin = min(KWIN_MAX, max(6 * nbc, 48))
+    delta = kwin - 3 * nbc - 1
+    if delta < 1:
+        kwin, delta = 3 * nbc + 2, 1
+    nchain = (npairs + nbc - 1) // nbc
+    S = (kwin + delta + 3 * nbc + 2 + delta - 1) // delta
+    nbs = [min(nbc, npairs - c * nbc) for c in range(nchain)]
+    tend = [(hi - lo - 1) + 3 * (nbs[c] - 1) for c in range(nchain)]
+    last = max(c * S + (tend[c] + delta) // delta for c in range(nchain))
+    for s in range(last):
+        for c in range(nchain):
+            if s < c * S:
+                continue
+            tau0 = (s - c * S) * delta
+            if tau0 > tend[c]:
+                continue
+            tau1 = min(tau0 + delta, tend[c] + 1)
+            nb = nbs[c]
+            kmin, kmax = max(lo, lo + tau0 - 3 * (nb - 1)), min(hi - 1, lo + tau1 - 1)
+            if kmin > kmax:
+                continue
+            ws = lo if kmin == lo else kmin - 1
+            we = min(kmax + 3, hi)
+            yield ws, we, tau0, tau1, nb, delta
+
+
+def pattern(lo, hi, ws, we, tau0, tau1, nb):
+    L = we - ws + 1
+    P = np.eye(L, dtype=bool)
+    for tau in range(tau0, tau1):
+        for j in range(nb):            # bottom bulge first, as in the chase
+            k = lo + tau - 3 * j
+            if lo <= k <= hi - 1:
+                nr = min(3, hi - k + 1)
+                kl = k - ws
+                rows = P[:, kl:kl + nr].any(axis=1)
+                P[np.ix_(rows, np.arange(kl, kl + nr))] = True
+    return P
+
+
+@pytest.mark.parametrize("n,npairs,nbc", [(300, 8, 4), (400, 30, 10), (260, 4, 1), (500, 64, 32), (700, 48, 24)])
+def test_chase_transform_band(n, npairs, nbc):
+    for ws, we, tau0, tau1, nb, delta in schedule(0, n - 1, npairs, nbc):
+        P = pattern(0, n - 1, ws, we, tau0, tau1, nb)
+        r, c = np.nonzero(P)
+        assert np.max(r - c) <= 2 + 2 * min(nb - 1, delta - 1)
+        assert np.max(c - r) <= delta + 1

@@ -89,6 +89,9 @@ def test_apply_u_matches_product(k, m, side):
     (200, 10, 180, 12, 4),
     (300, 0, 299, 16, 16),
     (500, 50, 499, 24, 6),
+    (600, 0, 599, 64, 32),
+    (700, 20, 690, 48, 24),
+    (400, 0, 399, 30, 10),
 ])
 def test_sweep_matches_oracle(n, lo, hi, npairs, nbc):
     """Windowed multi-chain bulge chase (Sec. 2.3/2.4) vs the oracle's direct
