@@ -257,15 +257,23 @@ __device__ inline bool subdiag_negligible(const Mat& H, int k, int lo, int hi, c
   return ba * (ab * rs) <= fmax(sml, SCHUR_U * (bb * (aa * rs)));
 }
 
-// AED deflation test (Sec. 5.6) of the block of T ending at row j (size bs)
-// against spike entries sp_j (and sp_{j-1} for bs == 2).
-__device__ inline bool spike_deflatable(const Mat& T, double spj, double spjm1, int j, int bs, const DeflParams& dp) {
+// AED deflation test (Sec. 5.6) of a diagonal block of size bs, given by
+// its entries [[a, b], [c, d]] (bs == 2) or d (bs == 1), against the spike
+// entries sp_j of its last row (and sp_{j-1} of the row above for bs == 2).
+__device__ inline bool spike_deflatable_blk(double a, double b, double c, double d, double spj, double spjm1, int bs,
+                                            const DeflParams& dp) {
   double s = (bs == 1) ? fabs(spj) : fmax(fabs(spj), fabs(spjm1));
   if (dp.mode == 1) return s <= SCHUR_U * dp.normH;
   if (dp.mode == 2) return s <= dp.thold;
-  if (bs == 1) return s <= fmax(smlnum_of(dp.n), SCHUR_U * fabs(T(j, j)));
-  double hhat = sqrt(fabs(T(j, j) * T(j - 1, j - 1))) + sqrt(fabs(T(j - 1, j) * T(j, j - 1)));
+  if (bs == 1) return s <= fmax(smlnum_of(dp.n), SCHUR_U * fabs(d));
+  double hhat = sqrt(fabs(d * a)) + sqrt(fabs(b * c));
   return s <= fmax(smlnum_of(dp.n), SCHUR_U * hhat);
+}
+
+// The same test for the block of T ending at row j.
+__device__ inline bool spike_deflatable(const Mat& T, double spj, double spjm1, int j, int bs, const DeflParams& dp) {
+  if (bs == 1) return spike_deflatable_blk(0.0, 0.0, 0.0, T(j, j), spj, spjm1, 1, dp);
+  return spike_deflatable_blk(T(j - 1, j - 1), T(j - 1, j), T(j, j - 1), T(j, j), spj, spjm1, 2, dp);
 }
 
 #endif  // __CUDACC__

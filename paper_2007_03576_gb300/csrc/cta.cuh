@@ -309,212 +309,393 @@ __device__ inline void small_qr_q(double W[4][2], int m, int q, double* Q) {
   }
 }
 
-// Warp 0 part of the swap (all 32 lanes call it).  Lane 0 solves the
-// Sylvester equation A11 X - X A22 = A12 (its Kronecker form, complete
-// pivoting by magnitude keys, a pivot below sml replaced by sml as Bai &
-// Demmel do for nearly equal eigenvalues) and factors [-X; I] = Q [R; 0];
-// lanes (a, b) then form D = Q^T A Q in parallel, D's (2,1) block is the
-// residual of the swap (accepted if <= max(10 u ||A||_F, nu n / u)) and is
-// set to zero.  Two 1x1 blocks [[a, b], [0, c]] swap by the rotation whose
-// first column is (b, c - a)/norm, which the Sylvester solution
-// x = b / (a - c) gives; its residual is zero by construction.
-// Results: sh->q (Q), sh->d (D), sh->iv[1] (1 = accepted).
-__device__ inline void warp_swap_compute(const Mat& T, int nT, int j, int p, int q, CtaShared* sh) {
-  const int lane = threadIdx.x & 31;
+// Factor of one swap, computed by one thread (each thread of a block may
+// compute a different swap).  Solves the Sylvester equation
+// A11 X - X A22 = A12 (its Kronecker form, complete pivoting by magnitude
+// keys, a pivot below sml replaced by sml as Bai & Demmel do for nearly equal
+// eigenvalues) and factors [-X; I] = Q [R; 0].  The swap is accepted when the
+// (2,1) block of Q^T A Q -- the part that must vanish -- is at most
+// max(10 u ||A||_F, nu n / u); the product itself is left to the caller.  Two
+// 1x1 blocks [[a, b], [0, c]] swap by the rotation whose first column is
+// (b, c - a)/norm, which the Sylvester solution x = b / (a - c) gives; its
+// residual is zero by construction.  Q (m x m, m = p + q) is written
+// column-major with leading dimension 4 to Qo.
+__device__ inline bool lane_swap_factor(const Mat& T, int nT, int j, int p, int q, double* Qo) {
   const int m = p + q;
-  double* Q = sh->q;
-  double* D = sh->d;
   if (p == 1 && q == 1) {
-    if (lane == 0) {
-      double a = T(j, j), b = T(j, j + 1), c = T(j + 1, j + 1);
-      double u0 = b, u1 = c - a;
-      double cs = 1.0, sn = 0.0;
-      if ((fm_abs_key(u0) | fm_abs_key(u1)) != 0) {
-        if (fm_safe_range3(u0, u1, 0.0)) {
-          double r = fast_rsqrt(fma(u0, u0, u1 * u1));
-          cs = u0 * r;
-          sn = u1 * r;
-        } else {
-          double r = hypot(u0, u1);
-          cs = u0 / r;
-          sn = u1 / r;
+    double a = T(j, j), b = T(j, j + 1), c = T(j + 1, j + 1);
+    double u0 = b, u1 = c - a;
+    double cs = 1.0, sn = 0.0;
+    if ((fm_abs_key(u0) | fm_abs_key(u1)) != 0) {
+      if (fm_safe_range3(u0, u1, 0.0)) {
+        double r = fast_rsqrt(fma(u0, u0, u1 * u1));
+        cs = u0 * r;
+        sn = u1 * r;
+      } else {
+        double r = hypot(u0, u1);
+        cs = u0 / r;
+        sn = u1 / r;
+      }
+    }
+    Qo[0] = cs; Qo[1] = sn; Qo[4] = -sn; Qo[5] = cs;
+    return true;
+  }
+  const int pq = p * q;
+  double K[4][4], rhs[4];
+  long long kmax = 0;
+  for (int c = 0; c < q; ++c)
+    for (int r = 0; r < p; ++r) {
+      int row = r + c * p;
+      rhs[row] = T(j + r, j + p + c);
+      for (int c2 = 0; c2 < q; ++c2)
+        for (int r2 = 0; r2 < p; ++r2) {
+          int col = r2 + c2 * p;
+          double v = ((c == c2) ? T(j + r, j + r2) : 0.0) - ((r == r2) ? T(j + p + c2, j + p + c) : 0.0);
+          K[row][col] = v;
+          long long kk = fm_abs_key(v);
+          kmax = kk > kmax ? kk : kmax;
+        }
+    }
+  double sml = fmax(SCHUR_U * __longlong_as_double(kmax), smlnum_of(nT));
+  long long smlk = fm_abs_key(sml);
+  int perm[4] = {0, 1, 2, 3};
+  double inv[4];
+  for (int i = 0; i < pq; ++i) {
+    int br = i, bc = i;
+    long long best = -1;
+    for (int r = i; r < pq; ++r)
+      for (int c = i; c < pq; ++c) {
+        long long kk = fm_abs_key(K[r][c]);
+        if (kk > best) {
+          best = kk;
+          br = r;
+          bc = c;
         }
       }
-      double t00 = fma(a, cs, b * sn), t01 = fma(-a, sn, b * cs);
-      double t10 = c * sn, t11 = c * cs;
-      D[0] = fma(cs, t00, sn * t10);
-      D[1] = 0.0;
-      D[4] = fma(cs, t01, sn * t11);
-      D[5] = fma(-sn, t01, cs * t11);
-      Q[0] = cs; Q[1] = sn; Q[4] = -sn; Q[5] = cs;
-      sh->iv[1] = 1;
+    if (br != i) {
+      for (int c = 0; c < pq; ++c) {
+        double t = K[i][c]; K[i][c] = K[br][c]; K[br][c] = t;
+      }
+      double t = rhs[i]; rhs[i] = rhs[br]; rhs[br] = t;
+    }
+    if (bc != i) {
+      for (int r = 0; r < pq; ++r) {
+        double t = K[r][i]; K[r][i] = K[r][bc]; K[r][bc] = t;
+      }
+      int t = perm[i]; perm[i] = perm[bc]; perm[bc] = t;
+    }
+    if (best < smlk) K[i][i] = sml;
+    inv[i] = fast_rcp(K[i][i]);
+    for (int r = i + 1; r < pq; ++r) {
+      double f = K[r][i] * inv[i];
+      for (int c = i + 1; c < pq; ++c) K[r][c] = fma(-f, K[i][c], K[r][c]);
+      rhs[r] = fma(-f, rhs[i], rhs[r]);
+    }
+  }
+  double y[4], x[4];
+  for (int i = pq - 1; i >= 0; --i) {
+    double s = rhs[i];
+    for (int c = i + 1; c < pq; ++c) s = fma(-K[i][c], y[c], s);
+    y[i] = s * inv[i];
+  }
+  for (int i = 0; i < pq; ++i) x[perm[i]] = y[i];
+  double W[4][2];
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < 2; ++c) W[r][c] = 0.0;
+  for (int c = 0; c < q; ++c) {
+    for (int r = 0; r < p; ++r) W[r][c] = -x[r + c * p];
+    W[p + c][c] = 1.0;
+  }
+  double Q[16];
+  small_qr_q(W, m, q, Q);
+  // residual: rows q..m-1, columns 0..q-1 of Q^T A Q
+  double res = 0.0, fro = 0.0;
+  for (int b = 0; b < q; ++b) {
+    double aq[4];
+    for (int t = 0; t < m; ++t) {
+      double acc = 0.0;
+      for (int s2 = 0; s2 < m; ++s2) acc = fma(T(j + t, j + s2), Q[s2 + 4 * b], acc);
+      aq[t] = acc;
+    }
+    for (int a = q; a < m; ++a) {
+      double d = 0.0;
+      for (int t = 0; t < m; ++t) d = fma(Q[t + 4 * a], aq[t], d);
+      res = fma(d, d, res);
+    }
+  }
+  for (int t = 0; t < m; ++t)
+    for (int s2 = 0; s2 < m; ++s2) {
+      double av = T(j + t, j + s2);
+      fro = fma(av, av, fro);
+    }
+  for (int b = 0; b < m; ++b)
+    for (int a = 0; a < m; ++a) Qo[a + 4 * b] = Q[a + 4 * b];
+  const double tol = 10.0 * SCHUR_U;
+  return res <= fmax(tol * tol * fro, sml * sml);
+}
+
+// ---------------------------------------------------------------------------
+// Deflation checks and reordering of AED step 2 (Sec. 2.5), pipelined.
+//
+// The sequential procedure checks the bottom unevaluated block; a block that
+// fails is moved by adjacent swaps to just below the blocks that failed
+// before it, and the next bottom block is checked.  A failed block's later
+// swaps act on rows and columns above the blocks that are still to be
+// checked, so they can run while those are checked, and swaps of disjoint
+// pairs of adjacent blocks commute.  Here every failed block that still has
+// an unevaluated block directly above it swaps with that block in each round,
+// and the bottom block is checked in the same round when it is unevaluated:
+// the same swaps and checks as in the sequential order, each failed block
+// moving up one block per round behind the one before it.  Per round, one
+// thread computes each swap's factor, then warps apply the factors to the rows
+// (left products, disjoint rows) and, after a barrier, to the columns of T and
+// V (right products, disjoint columns).  A checked 2x2 block is tested in its
+// standardised form (computed by the checking thread); the standardising
+// rotation is applied when the block deflates, or splits into two 1x1 blocks.
+// A rejected swap ends the reordering (the blocks stay where they are and
+// count as undeflated), as the sequential procedure halts.
+// ---------------------------------------------------------------------------
+#define DEFL_MAX_OPS 48       // swaps per round (further ones wait a round)
+#define DEFL_MAX_BLOCKS 1024  // diagonal blocks of a window (nw <= 1024)
+
+struct DeflState {
+  unsigned char bsz[DEFL_MAX_BLOCKS];  // block sizes of rows [info, ns), top to bottom
+  unsigned char bst[DEFL_MAX_BLOCKS];  // 0 not yet checked, 1 failed its check
+  double Q[DEFL_MAX_OPS][16];          // the round's swap factors
+  int opj[DEFL_MAX_OPS];               // first row of the pair
+  int opk[DEFL_MAX_OPS];               // list index of the pair's upper block
+  unsigned char opp[DEFL_MAX_OPS], opq[DEFL_MAX_OPS], opacc[DEFL_MAX_OPS];
+  double rot[6];                       // cs, sn and the standardised block of the checked 2x2 block
+  int nblk, ns, nops, chk, rot_k, halt, done;
+};
+
+// Warp 0: this round's swaps (pairs "unevaluated above failed") and whether
+// the bottom block is checked.
+__device__ inline void defl_schedule(int info, DeflState* ds) {
+  const int lane = threadIdx.x & 31;
+  const int nb = ds->nblk;
+  const int per = (nb + 31) / 32;
+  const int k0 = min(lane * per, nb), k1 = min(k0 + per, nb);
+  int rows = 0, pairs = 0;
+  for (int k = k0; k < k1; ++k) {
+    rows += ds->bsz[k];
+    if (k > 0 && ds->bst[k] == 1 && ds->bst[k - 1] == 0) ++pairs;
+  }
+  int rs = rows, ps = pairs;
+  for (int o = 1; o < 32; o <<= 1) {
+    int a = __shfl_up_sync(0xffffffffu, rs, o);
+    int b = __shfl_up_sync(0xffffffffu, ps, o);
+    if (lane >= o) {
+      rs += a;
+      ps += b;
+    }
+  }
+  int pos = info + rs - rows, op = ps - pairs;
+  for (int k = k0; k < k1; ++k) {
+    if (k > 0 && ds->bst[k] == 1 && ds->bst[k - 1] == 0) {
+      if (op < DEFL_MAX_OPS) {
+        int p = ds->bsz[k - 1];
+        ds->opj[op] = pos - p;
+        ds->opk[op] = k - 1;
+        ds->opp[op] = (unsigned char)p;
+        ds->opq[op] = ds->bsz[k];
+      }
+      ++op;
+    }
+    pos += ds->bsz[k];
+  }
+  const int total = __shfl_sync(0xffffffffu, ps, 31);
+  if (lane == 0) {
+    const int nops = min(total, DEFL_MAX_OPS);
+    const int chk = (nb > 0 && ds->bst[nb - 1] == 0) ? 1 : 0;
+    ds->nops = nops;
+    ds->chk = chk;
+    ds->rot_k = -1;
+    ds->done = (nops == 0 && !chk) ? 1 : 0;
+  }
+}
+
+// The checking thread: bottom block of rows [info, ns).
+__device__ inline void defl_check(const Mat& T, double s, const Mat& V, const DeflParams& dp, DeflState* ds) {
+  const int nb = ds->nblk, ns = ds->ns;
+  const int bs = ds->bsz[nb - 1];
+  const int jb = ns - 1;
+  if (bs == 1) {
+    bool defl = spike_deflatable_blk(0.0, 0.0, 0.0, T(jb, jb), s * V(0, jb), 0.0, 1, dp);
+    if (defl) {
+      ds->nblk = nb - 1;
+      ds->ns = ns - 1;
+    } else {
+      ds->bst[nb - 1] = 1;
     }
     return;
   }
-  if (lane == 0) {
-    int pq = p * q;
-    double K[4][4], rhs[4];
-    long long kmax = 0;
-    for (int c = 0; c < q; ++c)
-      for (int r = 0; r < p; ++r) {
-        int row = r + c * p;
-        rhs[row] = T(j + r, j + p + c);
-        for (int c2 = 0; c2 < q; ++c2)
-          for (int r2 = 0; r2 < p; ++r2) {
-            int col = r2 + c2 * p;
-            double v = ((c == c2) ? T(j + r, j + r2) : 0.0) - ((r == r2) ? T(j + p + c2, j + p + c) : 0.0);
-            K[row][col] = v;
-            long long kk = fm_abs_key(v);
-            kmax = kk > kmax ? kk : kmax;
-          }
-      }
-    double sml = fmax(SCHUR_U * __longlong_as_double(kmax), smlnum_of(nT));
-    long long smlk = fm_abs_key(sml);
-    int perm[4] = {0, 1, 2, 3};
-    double inv[4];
-    for (int i = 0; i < pq; ++i) {
-      int br = i, bc = i;
-      long long best = -1;
-      for (int r = i; r < pq; ++r)
-        for (int c = i; c < pq; ++c) {
-          long long kk = fm_abs_key(K[r][c]);
-          if (kk > best) {
-            best = kk;
-            br = r;
-            bc = c;
-          }
-        }
-      if (br != i) {
-        for (int c = 0; c < pq; ++c) {
-          double t = K[i][c]; K[i][c] = K[br][c]; K[br][c] = t;
-        }
-        double t = rhs[i]; rhs[i] = rhs[br]; rhs[br] = t;
-      }
-      if (bc != i) {
-        for (int r = 0; r < pq; ++r) {
-          double t = K[r][i]; K[r][i] = K[r][bc]; K[r][bc] = t;
-        }
-        int t = perm[i]; perm[i] = perm[bc]; perm[bc] = t;
-      }
-      if (best < smlk) K[i][i] = sml;
-      inv[i] = fast_rcp(K[i][i]);
-      for (int r = i + 1; r < pq; ++r) {
-        double f = K[r][i] * inv[i];
-        for (int c = i + 1; c < pq; ++c) K[r][c] = fma(-f, K[i][c], K[r][c]);
-        rhs[r] = fma(-f, rhs[i], rhs[r]);
-      }
-    }
-    double y[4], x[4];
-    for (int i = pq - 1; i >= 0; --i) {
-      double s = rhs[i];
-      for (int c = i + 1; c < pq; ++c) s = fma(-K[i][c], y[c], s);
-      y[i] = s * inv[i];
-    }
-    for (int i = 0; i < pq; ++i) x[perm[i]] = y[i];
-    double W[4][2];
-    for (int r = 0; r < m; ++r)
-      for (int c = 0; c < 2; ++c) W[r][c] = 0.0;
-    for (int c = 0; c < q; ++c) {
-      for (int r = 0; r < p; ++r) W[r][c] = -x[r + c * p];
-      W[p + c][c] = 1.0;
-    }
-    small_qr_q(W, m, q, Q);
+  double cs, sn, B[4];
+  standardize2x2(T(jb - 1, jb - 1), T(jb - 1, jb), T(jb, jb - 1), T(jb, jb), cs, sn, B);
+  ds->rot[0] = cs;
+  ds->rot[1] = sn;
+  for (int t = 0; t < 4; ++t) ds->rot[2 + t] = B[t];
+  if (B[2] == 0.0) {
+    // real pair: two 1x1 blocks, checked from the next round on
+    ds->rot_k = jb - 1;
+    ds->bsz[nb - 1] = 1;
+    ds->bst[nb - 1] = 0;
+    ds->bsz[nb] = 1;
+    ds->bst[nb] = 0;
+    ds->nblk = nb + 1;
+    return;
   }
-  __syncwarp();
-  // D = Q^T A Q, one entry per lane
-  const int a = lane & 3, b = lane >> 2;
-  const bool mine = lane < 16 && a < m && b < m;
-  double dab = 0.0, fro = 0.0;
-  if (mine) {
-    for (int t = 0; t < m; ++t) {
-      double aq = 0.0;
-      for (int s2 = 0; s2 < m; ++s2) aq = fma(T(j + t, j + s2), Q[s2 + 4 * b], aq);
-      dab = fma(Q[t + 4 * a], aq, dab);
-    }
-    double av = T(j + a, j + b);
-    fro = av * av;
-  }
-  double res = (mine && a >= q && b < q) ? dab * dab : 0.0;
-  for (int o = 16; o > 0; o >>= 1) {
-    res += __shfl_xor_sync(0xffffffffu, res, o);
-    fro += __shfl_xor_sync(0xffffffffu, fro, o);
-  }
-  if (mine) D[a + 4 * b] = (a >= q && b < q) ? 0.0 : dab;
-  if (lane == 0) {
-    double tol = 10.0 * SCHUR_U;
-    double sml = smlnum_of(nT);
-    sh->iv[1] = (res <= fmax(tol * tol * fro, sml * sml)) ? 1 : 0;
+  const double v0 = V(0, jb - 1), v1 = V(0, jb);
+  const double w0 = fma(cs, v0, sn * v1), w1 = fma(-sn, v0, cs * v1);
+  bool defl = spike_deflatable_blk(B[0], B[1], B[2], B[3], s * w1, s * w0, 2, dp);
+  if (defl) {
+    ds->rot_k = jb - 1;
+    ds->nblk = nb - 1;
+    ds->ns = ns - 2;
+  } else {
+    ds->bst[nb - 1] = 1;
   }
 }
 
-// Swap the adjacent blocks (sizes p, q) starting at row j of the nT x nT
-// quasi-triangular T, accumulating into V (vrows x nT).  Returns false (T, V
-// untouched) when the swap is rejected.  The swapped blocks are left as the
-// orthogonal factor produces them (not re-standardised: callers standardise
-// a block when its standard form is needed).  Two barriers: the diagonal
-// block is written from D while the other threads apply Q to the rest of the
-// rows (columns >= j+m), the rest of the columns (rows < j) and V.
-__device__ inline bool cta_swap(const Mat& T, int nT, int j, int p, int q, const Mat& V, int vrows, CtaShared* sh) {
-  if (cta_tid() < 32) warp_swap_compute(T, nT, j, p, q, sh);
+// y = Q^T x on rows j..j+M-1 of the columns c of T (lanes over columns).
+template <int M>
+__device__ __forceinline__ void defl_left(const Mat& T, int nT, int j, const double* Q, int lane) {
+  for (int c = j + lane; c < nT; c += 32) {
+    double x[M];
+#pragma unroll
+    for (int t = 0; t < M; ++t) x[t] = T(j + t, c);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 0; t < M; ++t) acc = fma(Q[t + 4 * a], x[t], acc);
+      T(j + a, c) = acc;
+    }
+  }
+}
+
+// x Q on columns j..j+M-1 of rows 0..j+M-1 of T and of all vrows rows of V;
+// rows j+q.. of T get exact zeros in columns j..j+q-1 (the swap's residual).
+template <int M>
+__device__ __forceinline__ void defl_right(const Mat& T, const Mat& V, int vrows, int j, int q, const double* Q,
+                                           int lane) {
+  const int nr = j + M;
+  for (int it = lane; it < nr + vrows; it += 32) {
+    const bool onT = it < nr;
+    const Mat& X = onT ? T : V;
+    const int r = onT ? it : it - nr;
+    double x[M];
+#pragma unroll
+    for (int t = 0; t < M; ++t) x[t] = X(r, j + t);
+    const bool low = onT && r >= j + q;
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 0; t < M; ++t) acc = fma(x[t], Q[t + 4 * b], acc);
+      X(r, j + b) = (low && b < q) ? 0.0 : acc;
+    }
+  }
+}
+
+// Runs the checks and the reordering on rows [info, nw) of T (V: the
+// accumulated transform, vrows rows).  Returns ns (rows ns..nw-1 deflated);
+// failed = 1 when a swap was rejected (or the round limit was reached).
+__device__ inline int cta_aed_deflate(const Mat& T, int nw, int info, double s, const Mat& V, int vrows,
+                                      const DeflParams& dp, int& failed) {
+  __shared__ DeflState ds;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  if (tid == 0) {
+    int nb = 0;
+    for (int j = info; j < nw;) {
+      int b = (j + 1 < nw && T(j + 1, j) != 0.0) ? 2 : 1;
+      ds.bsz[nb] = (unsigned char)b;
+      ds.bst[nb] = 0;
+      ++nb;
+      j += b;
+    }
+    ds.nblk = nb;
+    ds.ns = nw;
+    ds.halt = 0;
+  }
   __syncthreads();
-  if (sh->iv[1] == 0) {
+  const int max_rounds = 4 * nw + 16;
+  int round = 0;
+  for (; round < max_rounds; ++round) {
+    if (tid < 32) defl_schedule(info, &ds);
     __syncthreads();
-    return false;
-  }
-  const int m = p + q;
-  const double* Q = sh->q;
-  const int nrest_c = nT - (j + m);  // columns right of the block
-  const int nrest_r = j;             // rows above the block
-  const int total = nrest_c + nrest_r + vrows + 1;
-  for (int it = cta_tid(); it < total; it += cta_nt()) {
-    double x[4], y[4];
-    if (it < nrest_c) {
-      int c = j + m + it;
-      for (int t = 0; t < m; ++t) x[t] = T(j + t, c);
-      for (int a = 0; a < m; ++a) {
-        double s = 0.0;
-        for (int t = 0; t < m; ++t) s += Q[t + 4 * a] * x[t];
-        y[a] = s;
+    if (ds.done || ds.halt) break;
+    const int nops = ds.nops;
+    if (tid < nops) {
+      const int j = ds.opj[tid], p = ds.opp[tid], q = ds.opq[tid];
+      const bool acc = lane_swap_factor(T, nw, j, p, q, ds.Q[tid]);
+      ds.opacc[tid] = acc ? 1 : 0;
+      if (acc) {
+        const int k = ds.opk[tid];
+        ds.bsz[k] = (unsigned char)q;
+        ds.bsz[k + 1] = (unsigned char)p;
+        ds.bst[k] = 1;
+        ds.bst[k + 1] = 0;
+      } else {
+        ds.halt = 1;
       }
-      for (int t = 0; t < m; ++t) T(j + t, c) = y[t];
-    } else if (it < nrest_c + nrest_r) {
-      int r = it - nrest_c;
-      for (int t = 0; t < m; ++t) x[t] = T(r, j + t);
-      for (int b = 0; b < m; ++b) {
-        double s = 0.0;
-        for (int t = 0; t < m; ++t) s += x[t] * Q[t + 4 * b];
-        y[b] = s;
-      }
-      for (int t = 0; t < m; ++t) T(r, j + t) = y[t];
-    } else if (it < nrest_c + nrest_r + vrows) {
-      int r = it - nrest_c - nrest_r;
-      for (int t = 0; t < m; ++t) x[t] = V(r, j + t);
-      for (int b = 0; b < m; ++b) {
-        double s = 0.0;
-        for (int t = 0; t < m; ++t) s += x[t] * Q[t + 4 * b];
-        y[b] = s;
-      }
-      for (int t = 0; t < m; ++t) V(r, j + t) = y[t];
-    } else {
-      for (int a = 0; a < m; ++a)
-        for (int b = 0; b < m; ++b) T(j + a, j + b) = sh->d[a + 4 * b];
     }
+    if (tid == (int)blockDim.x - 1 && ds.chk) defl_check(T, s, V, dp, &ds);
+    __syncthreads();
+    const int rk = ds.rot_k;
+    const double cs = ds.rot[0], sn = ds.rot[1];
+    const bool rot = rk >= 0 && !(cs == 1.0 && sn == 0.0);
+    // left products (rows of each pair / of the rotated block)
+    for (int o = warp; o <= nops; o += nwarps) {
+      if (o < nops) {
+        if (!ds.opacc[o]) continue;
+        const int j = ds.opj[o], m = ds.opp[o] + ds.opq[o];
+        if (m == 2) defl_left<2>(T, nw, j, ds.Q[o], lane);
+        else if (m == 3) defl_left<3>(T, nw, j, ds.Q[o], lane);
+        else defl_left<4>(T, nw, j, ds.Q[o], lane);
+      } else if (rot) {
+        for (int c = rk + 2 + lane; c < nw; c += 32) {
+          double a = T(rk, c), b = T(rk + 1, c);
+          T(rk, c) = fma(cs, a, sn * b);
+          T(rk + 1, c) = fma(-sn, a, cs * b);
+        }
+      }
+    }
+    __syncthreads();
+    // right products (columns of each pair / of the rotated block, T and V)
+    for (int o = warp; o <= nops; o += nwarps) {
+      if (o < nops) {
+        if (!ds.opacc[o]) continue;
+        const int j = ds.opj[o], q = ds.opq[o], m = ds.opp[o] + q;
+        if (m == 2) defl_right<2>(T, V, vrows, j, q, ds.Q[o], lane);
+        else if (m == 3) defl_right<3>(T, V, vrows, j, q, ds.Q[o], lane);
+        else defl_right<4>(T, V, vrows, j, q, ds.Q[o], lane);
+      } else if (rk >= 0) {
+        if (rot) {
+          for (int it = lane; it < rk + vrows; it += 32) {
+            const bool onT = it < rk;
+            const Mat& X = onT ? T : V;
+            const int r = onT ? it : it - rk;
+            double a = X(r, rk), b = X(r, rk + 1);
+            X(r, rk) = fma(cs, a, sn * b);
+            X(r, rk + 1) = fma(-sn, a, cs * b);
+          }
+        }
+        if (lane == 0) {
+          T(rk, rk) = ds.rot[2];
+          T(rk, rk + 1) = ds.rot[3];
+          T(rk + 1, rk) = ds.rot[4];
+          T(rk + 1, rk + 1) = ds.rot[5];
+        }
+      }
+    }
+    __syncthreads();
   }
+  const int ns = ds.ns;
+  failed = (ds.halt || round >= max_rounds) ? 1 : 0;
   __syncthreads();
-  return true;
-}
-
-// Move the block of size p starting at ifst up to start at ilst (a block
-// boundary) by adjacent swaps; false if a swap was rejected.
-__device__ inline bool cta_move_block_up(const Mat& T, int nT, int ifst, int ilst, int p, const Mat& V, int vrows,
-                                         CtaShared* sh) {
-  int here = ifst;
-  while (here > ilst) {
-    int q = (here >= 2 && here - 2 >= ilst && T(here - 1, here - 2) != 0.0) ? 2 : 1;
-    if (!cta_swap(T, nT, here - q, q, p, V, vrows, sh)) return false;
-    here -= q;
-  }
-  return true;
+  return ns;
 }
 
 // ---------------------------------------------------------------------------
@@ -609,36 +790,8 @@ __device__ inline int cta_aed_post(const Mat& T, int nw, int info, double s, con
                                    double* vbuf, double* cand_re, double* cand_im, int* ncand_out, double* top_out,
                                    int* swap_fail_out, CtaShared* sh, long long* cyc = nullptr) {
   long long c0 = clock64();
-  int ns = nw;
-  int ilst = info;
   int failed = 0;
-  for (int guard = 0; guard < 2 * nw + 2 && ilst < ns; ++guard) {
-    // the bottom 2x2 block is put in standard form before it is tested
-    // (swaps leave moved blocks unstandardised)
-    if (ns >= 2 && T(ns - 1, ns - 2) != 0.0) cta_standardize_block(T, ns - 2, nw, V, nw, sh);
-    // decision by thread 0
-    if (cta_tid() == 0) {
-      int bs = (ns >= 2 && T(ns - 1, ns - 2) != 0.0) ? 2 : 1;
-      double spj = s * V(0, ns - 1);
-      double spm = (bs == 2) ? s * V(0, ns - 2) : 0.0;
-      bool defl = spike_deflatable(T, spj, spm, ns - 1, bs, dp);
-      sh->iv[2] = bs;
-      sh->iv[3] = defl ? 1 : 0;
-    }
-    __syncthreads();
-    int bs = sh->iv[2];
-    bool defl = sh->iv[3] != 0;
-    __syncthreads();
-    if (defl) {
-      ns -= bs;
-      continue;
-    }
-    if (!cta_move_block_up(T, nw, ns - bs, ilst, bs, V, nw, sh)) {
-      failed = 1;
-      break;
-    }
-    ilst += bs;
-  }
+  int ns = cta_aed_deflate(T, nw, info, s, V, nw, dp, failed);
   int nd = nw - ns;
   long long c1 = clock64();
   // candidates of the undeflated part (converged rows info..ns-1)

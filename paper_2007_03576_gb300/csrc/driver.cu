@@ -227,11 +227,19 @@ void init_kernel_attributes() {
   int dev = 0;
   ck(cudaGetDevice(&dev));
   ck(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
-  const int big = 220 * 1024;
-  ck(cudaFuncSetAttribute(k_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  ck(cudaFuncSetAttribute(k_smallqr, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  ck(cudaFuncSetAttribute(k_aed_small, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  ck(apply_u_set_smem(big));
+  // each kernel may take what the block limit leaves beside its static
+  // shared memory
+  int optin = 0;
+  ck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  auto allow = [&](const void* k) {
+    cudaFuncAttributes fa;
+    ck(cudaFuncGetAttributes(&fa, k));
+    ck(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+  };
+  allow((const void*)k_chase);
+  allow((const void*)k_smallqr);
+  allow((const void*)k_aed_small);
+  ck(apply_u_set_smem(220 * 1024));
   g_attr_done = true;
 }
 
