@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -190,12 +191,21 @@ void PhaseTimer::end(cudaStream_t st, int token) {
   ck(cudaEventRecord(pool[2 * token + 1], st));
 }
 
+void PhaseTimer::collect(size_t i) {
+  float t = 0.f;
+  if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) ms[phase_of[i]] += t;
+  if (trace && base) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, *base, pool[2 * i]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, *base, pool[2 * i + 1]) == cudaSuccess)
+      trace->push_back({(double)sid, (double)phase_of[i], (double)a, (double)b});
+  }
+  cudaGetLastError();
+}
+
 void PhaseTimer::flush() {
   if (depth > 0) return;  // a bracket is still open: its end event is not recorded yet
-  for (size_t i = 0; i < used; ++i) {
-    float t = 0.f;
-    if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) ms[phase_of[i]] += t;
-  }
+  for (size_t i = 0; i < used; ++i) collect(i);
   used = 0;
 }
 
@@ -203,8 +213,7 @@ void PhaseTimer::flush_completed() {
   size_t i = 0;
   for (; i < used; ++i) {
     if (cudaEventQuery(pool[2 * i + 1]) != cudaSuccess) break;
-    float t = 0.f;
-    if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) ms[phase_of[i]] += t;
+    collect(i);
   }
   cudaGetLastError();
   if (i == 0) return;
@@ -261,10 +270,13 @@ Solver::Solver(const schur_opts* o) {
 }
 
 Solver::~Solver() {
-  if (zst) {
-    cudaStreamSynchronize(zst);
-    cudaStreamDestroy(zst);
-  }
+  for (cudaStream_t x : {zst, sst, own_st})
+    if (x) {
+      cudaStreamSynchronize(x);
+      cudaStreamDestroy(x);
+    }
+  for (cudaEvent_t e : {ev_t1, ev_t2, ev_join, ev_base})
+    if (e) cudaEventDestroy(e);
   for (auto& r : live)
     if (r.ev) cudaEventDestroy(r.ev);
   for (auto& e : spare_events) cudaEventDestroy(e);
@@ -274,15 +286,57 @@ Solver::~Solver() {
   if (owned) cudaFree(owned);
 }
 
-// Second stream for Z (level 0).  Lowest priority so that the critical path
-// (chase, AED, H updates) gets the SMs first.
-void Solver::init_zstream() {
-  int lo = 0, hi = 0;
-  ck(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-  ck(cudaStreamCreateWithPriority(&zst, cudaStreamNonBlocking, lo));
-  ck(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
-  ck(cudaEventCreateWithFlags(&ev_zdone, cudaEventDisableTiming));
-  ztimer.on = timer.on;
+// Streams of a full reduction (level 0); st becomes the call's own stream.
+void Solver::init_streams(bool with_z) {
+  int least = 0, greatest = 0;
+  ck(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  ck(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+  ck(cudaEventCreateWithFlags(&ev_t1, cudaEventDisableTiming));
+  ck(cudaEventCreateWithFlags(&ev_t2, cudaEventDisableTiming));
+  ck(cudaStreamCreateWithPriority(&own_st, cudaStreamNonBlocking, greatest));
+  // one level below the main stream, so that a chase step's blocks are
+  // placed before the side stream's
+  ck(cudaStreamCreateWithPriority(&sst, cudaStreamNonBlocking, greatest < least ? greatest + 1 : greatest));
+  ust = st;
+  ck(cudaEventRecord(ev_join, ust));
+  ck(cudaStreamWaitEvent(own_st, ev_join, 0));
+  st = own_st;
+  trace_path = getenv("SCHUR_TRACE");
+  if (trace_path && *trace_path) {
+    timer.on = true;
+    ck(cudaEventCreate(&ev_base));
+    ck(cudaEventRecord(ev_base, st));
+    PhaseTimer* ts[3] = {&timer, &ztimer, &stimer};
+    for (int k = 0; k < 3; ++k) {
+      ts[k]->sid = k;
+      ts[k]->base = &ev_base;
+      ts[k]->trace = &trace;
+    }
+  } else {
+    trace_path = nullptr;
+  }
+  stimer.on = timer.on;
+  if (with_z) {
+    ck(cudaStreamCreateWithPriority(&zst, cudaStreamNonBlocking, least));
+    ck(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
+    ck(cudaEventCreateWithFlags(&ev_zdone, cudaEventDisableTiming));
+    ztimer.on = timer.on;
+  }
+}
+
+void Solver::write_trace() {
+  if (!trace_path) return;
+  FILE* f = fopen(trace_path, "w");
+  if (!f) return;
+  fprintf(f, "stream,phase,start_ms,end_ms\n");
+  for (auto& r : trace) fprintf(f, "%d,%d,%.4f,%.4f\n", (int)r[0], (int)r[1], r[2], r[3]);
+  fclose(f);
+}
+
+void Solver::join_caller() {
+  if (!own_st) return;
+  ck(cudaEventRecord(ev_join, st));
+  ck(cudaStreamWaitEvent(ust, ev_join, 0));
 }
 
 // Regions of the arena are handed out in order, wrapping at the end; a new
@@ -300,6 +354,8 @@ double* Solver::arena_alloc(size_t n) {
   int last = -1;
   for (size_t i = 0; i < live.size(); ++i)
     if (live[i].a < b && a < live[i].b) last = (int)i;
+  // the side stream may still read the last chase step's region
+  if (t2_pending && t2_a < b && a < t2_b) ck(cudaStreamWaitEvent(st, ev_t2, 0));
   for (int i = 0; i <= last; ++i) {
     Region r = live.front();
     live.pop_front();
@@ -384,6 +440,7 @@ void Solver::read_ctl(const Ctl* dctl) {
   ck(cudaStreamSynchronize(st));
   timer.flush();
   if (zst) ztimer.flush_completed();
+  if (sst) stimer.flush_completed();
 }
 
 DeflParams Solver::defl(int n) const {
@@ -398,8 +455,9 @@ DeflParams Solver::defl(int n) const {
 // Issue a list of off-window products (split in launches of at most
 // MAX_UPD_TASKS tasks; tasks within a launch must not overlap).
 void Solver::run_updates(std::vector<UpdTask>& tasks, cudaStream_t sarg, bool on_z) {
-  cudaStream_t s = on_z ? sarg : st;
-  PhaseTimer& tm = on_z ? ztimer : timer;
+  const bool on_side = !on_z && sarg != nullptr && sarg == sst;
+  cudaStream_t s = (on_z || on_side) ? sarg : st;
+  PhaseTimer& tm = on_z ? ztimer : (on_side ? stimer : timer);
   const int phase = on_z ? PH_Z : cur_update_phase;
   size_t i = 0;
   while (i < tasks.size()) {
@@ -439,6 +497,10 @@ void Solver::run_updates(std::vector<UpdTask>& tasks, cudaStream_t sarg, bool on
     // streams compete the block scheduler can hand freed SMs to the
     // high-priority stream (H updates, chase, AED) between tiles
     int grid = std::min(tile, 1 << 20);
+    // the side stream's products leave SMs free for the chase step that
+    // runs beside them
+    if (on_side && side_reserve > 0)
+      grid = std::min(grid, apply_u_blocks_per_sm(tn, smem) * std::max(1, num_sms() - side_reserve));
     int tok = tm.begin(s, phase);
     ++g_stats.kernel_launches;
     ck(launch_apply_u(tn, grid, smem, s, a));
@@ -525,6 +587,9 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
   }
   size_t smem = chase_smem_bytes(kwin);
   const bool zasync = (lev == 0 && zst != nullptr && M.Z != nullptr);
+  const bool side = (lev == 0 && sst != nullptr);
+  const bool use_arena = zasync || side;
+  side_reserve = std::min(nchain, MAX_CHAINS) + 2;
   for (int s = 0; s < last; ++s) {
     ChaseArgs a;
     memset(&a, 0, sizeof(a));
@@ -555,10 +620,10 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
     }
     if (na == 0) continue;
     a.nchain = na;
-    // this step's window transforms: from the arena while the Z stream may
-    // still need them, else the level's buffer
+    // this step's window transforms: from the arena while the Z or the side
+    // stream may still need them, else the level's buffer
     const size_t need = (size_t)na * kwin * kwin;
-    double* ubase = zasync ? arena_alloc(need) : Lv.ubuf;
+    double* ubase = use_arena ? arena_alloc(need) : Lv.ubuf;
     int tok = timer.begin(st, PH_CHASE);
     ++g_stats.kernel_launches;
     k_chase<<<na, CTA_THREADS, smem, st>>>(M.H, M.ldh, dpairs, ubase, a);
@@ -587,8 +652,31 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
       }
     }
     if (zasync) z_defer(tz, ubase, need);   // issued on zst at the end of the sweep
-    run_updates(t1);
-    run_updates(t2);
+    else if (use_arena) arena_release(ubase, need, false);
+    if (side) {
+      // t1 meets the previous step's t2 where a chain's rows cross the
+      // columns of the chain ahead of it
+      if (t2_pending) ck(cudaStreamWaitEvent(st, ev_t2, 0));
+      run_updates(t1);
+      if (!t2.empty()) {
+        ck(cudaEventRecord(ev_t1, st));
+        ck(cudaStreamWaitEvent(sst, ev_t1, 0));
+        run_updates(t2, sst);
+        ck(cudaEventRecord(ev_t2, sst));
+        t2_pending = true;
+        t2_a = use_arena ? (size_t)(ubase - arena) : 0;
+        t2_b = use_arena ? t2_a + need : 0;
+      } else {
+        t2_pending = false;
+      }
+    } else {
+      run_updates(t1);
+      run_updates(t2);
+    }
+  }
+  if (t2_pending) {
+    ck(cudaStreamWaitEvent(st, ev_t2, 0));
+    t2_pending = false;
   }
   if (zasync) z_flush();
   if (lev == 0) {
@@ -803,20 +891,22 @@ extern "C" int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, d
     }
     Mat3 M{H, ldh, n, Z, ldz, n};
     s.cur_flops = &g_stats.sweep_gemm_flops;
-    if (Z) s.init_zstream();
+    s.init_streams(Z != nullptr);
     int info = s.qr_block(M, 0, 0, n - 1);
     s.drain_z();
     ++g_stats.kernel_launches;
     k_extract_eigs<<<std::max(1, std::min((n + 255) / 256, 4 * num_sms())), 256, 0, s.st>>>(H, ldh, n, wr, wi);
     ck(cudaGetLastError());
+    s.join_caller();
     ck(cudaStreamSynchronize(s.st));
     s.timer.flush();
     s.read_ctl(s.levels[0].ctl);
-    if (s.zst) {
-      ck(cudaStreamSynchronize(s.zst));
-      s.ztimer.flush_completed();
-      for (int ph = 0; ph < PH_COUNT; ++ph) s.timer.ms[ph] += s.ztimer.ms[ph];
-    }
+    for (cudaStream_t x : {s.zst, s.sst})
+      if (x) ck(cudaStreamSynchronize(x));
+    s.ztimer.flush_completed();
+    s.stimer.flush_completed();
+    for (int ph = 0; ph < PH_COUNT; ++ph) s.timer.ms[ph] += s.ztimer.ms[ph] + s.stimer.ms[ph];
+    s.write_trace();
     g_stats.aed_cycles_schur = (double)s.hctl->cyc_schur;
     g_stats.aed_cycles_post = (double)s.hctl->cyc_defl;
     g_stats.t_chase_ms = s.timer.ms[PH_CHASE];

@@ -10,6 +10,7 @@
 
 #define KWIN_MAX 112   // largest bulge-chase window (window + U in shared memory: 2 (k+1) k doubles)
 
+#include <array>
 #include <deque>
 
 namespace schur {
@@ -54,6 +55,12 @@ struct PhaseTimer {
   size_t used = 0;             // event pairs recorded since the last flush
   int depth = 0;               // > 0 while inside a timed region (nested launches not timed)
   double ms[PH_COUNT] = {0, 0, 0, 0, 0, 0};
+  // optional timeline: (stream id, phase, start ms, end ms) relative to
+  // *base, appended as pairs are collected
+  int sid = 0;
+  cudaEvent_t* base = nullptr;
+  std::vector<std::array<double, 4>>* trace = nullptr;
+  void collect(size_t i);
   int begin(cudaStream_t st, int phase);
   void end(cudaStream_t st, int token);
   void flush();                // after a stream synchronisation
@@ -81,6 +88,23 @@ struct Solver {
   // instead of competing with the sweep's own H updates.
   cudaStream_t zst = nullptr;
   PhaseTimer ztimer;
+  // At level 0 the call runs on its own streams, joined to the caller's
+  // stream (ust) by events at the start and the end: the main stream (st) at
+  // the greatest priority, zst at the least, and a side stream (sst, greatest
+  // priority) for each chase step's products on the rows above its windows,
+  // which nothing in the next chase step reads: they run beside it.
+  cudaStream_t ust = nullptr, own_st = nullptr, sst = nullptr;
+  PhaseTimer stimer;
+  cudaEvent_t ev_t1 = nullptr, ev_t2 = nullptr, ev_join = nullptr;
+  // SCHUR_TRACE=<file>: every timed bracket of the call is written there as
+  // "stream,phase,start_ms,end_ms" (streams 0 main, 1 Z, 2 side)
+  cudaEvent_t ev_base = nullptr;
+  std::vector<std::array<double, 4>> trace;
+  const char* trace_path = nullptr;
+  void write_trace();
+  bool t2_pending = false;   // ev_t2 recorded and not yet waited for by st
+  size_t t2_a = 0, t2_b = 0; // arena region [t2_a, t2_b) that the pending side-stream products read
+  int side_reserve = 0;      // SMs the side stream's products leave to the next chase step
   cudaEvent_t ev_ready = nullptr, ev_zdone = nullptr;
   // Circular arena (level 0) holding the chase U's and AED V's that the Z
   // stream has not consumed yet; a region is reused only after the event
@@ -115,7 +139,8 @@ struct Solver {
   void z_defer(std::vector<UpdTask>& tasks, const double* p, size_t n);  // held until z_flush
   void z_flush();                                                // issue zpending on zst after st's current point
   void drain_z();                                                // st waits for all of zst's work
-  void init_zstream();
+  void init_streams(bool with_z);                               // see ust / sst / zst
+  void join_caller();                                            // ust waits for st
   void sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs, int npairs, int nbc_req);
   int qr_block(const Mat3& M, int lev, int ilo, int ihi);
   int aed(const Mat3& M, int lev, int ktop, int kbot, int nw, int ns_max, int ndfl);

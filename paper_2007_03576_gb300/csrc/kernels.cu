@@ -464,6 +464,22 @@ cudaError_t launch_apply_u(int tn, int grid, size_t smem, cudaStream_t st, const
   return cudaGetLastError();
 }
 
+int apply_u_blocks_per_sm(int tn, size_t smem) {
+  int nb = 0;
+  cudaError_t e;
+  switch (tn) {
+    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_apply_u<64>, CTA_THREADS, smem); break;
+    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_apply_u<32>, CTA_THREADS, smem); break;
+    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_apply_u<16>, CTA_THREADS, smem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_apply_u<8>, CTA_THREADS, smem); break;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
 cudaError_t apply_u_set_smem(int bytes) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_apply_u<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;

@@ -25,6 +25,7 @@ __global__ void k_fastmath_eval(int n, const double* x, double* out);
 // off-window products (TN = vectors per tile, 64/32/16/8)
 cudaError_t launch_apply_u(int tn, int grid, size_t smem, cudaStream_t st, const UpdArgs& a);
 cudaError_t apply_u_set_smem(int bytes);
+int apply_u_blocks_per_sm(int tn, size_t smem);   // resident k_apply_u blocks per SM
 
 size_t chase_smem_bytes(int kwin);
 size_t apply_u_smem_bytes(int tn, int maxL);
