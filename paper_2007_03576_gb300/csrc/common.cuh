@@ -16,6 +16,8 @@
 
 // Bounds of the one-block kernels.
 #define CTA_THREADS 256
+#define CHASE_THREADS 512    // threads of a bulge-chase block (one warp per bulge or two)
+#define KWIN_MAX 112         // largest bulge-chase window (window + U in shared memory: 2 (k+1) k doubles)
 #define NW_SMEM_MAX 160      // AED windows / small blocks held in shared memory
 #define MAX_CHAINS 32        // bulge chains chased concurrently in one launch
 #define MAX_BULGES_PER_CHAIN 32

@@ -130,61 +130,113 @@ __device__ inline void cta_standardize_block(const Mat& T, int k, int ncols, con
 // ---------------------------------------------------------------------------
 // One Francis double-shift sweep on [l, i] of the m x m matrix T (full Schur
 // mode within T: columns up to m-1, rows from 0), accumulated into U.
-// Per reflector: thread 0 builds it (a short FP64 chain, see house3), then
-// the left product on rows k..k+2 and the right product on columns k..k+2
-// (and U) run over all threads, separated by a barrier because they meet on
-// the 3x3 diagonal block.
+//
+// One barrier per reflector.  The reflector of step k acts on rows k..k+2
+// (columns k..m-1) and on columns k..k+2 (rows 0..k+3 and U); the two
+// products meet only on the diagonal block (rows k..k+3, columns k..k+2).
+// Warp 0 updates that block and then builds the next step's reflector from
+// its first column (a short FP64 chain, see house3) -- the next reflector
+// needs nothing else -- while the other warps apply the current reflector to
+// the rest of rows k..k+2 and of columns k..k+2, which are disjoint.  Every
+// entry receives the same operations in the same order as with the left
+// product applied before the right one.  Reflectors alternate between two
+// slots of sh->r.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void refl3_apply(double* p, long long stride, int nr, double v1, double v2, double tau) {
+  double a0 = p[0], a1 = p[stride], a2 = (nr == 3) ? p[2 * stride] : 0.0;
+  double s = tau * fma(v2, a2, fma(v1, a1, a0));
+  p[0] = a0 - s;
+  p[stride] = fma(-s, v1, a1);
+  if (nr == 3) p[2 * stride] = fma(-s, v2, a2);
+}
+
 __device__ inline void cta_double_shift_sweep(const Mat& T, int m, int l, int i, double ssum, double sprod,
                                               const Mat& U, int urows, CtaShared* sh) {
+  const int tid = cta_tid(), nt = cta_nt(), lane = tid & 31;
+  if (tid == 0) {
+    const int nr = min(3, i - l + 1);
+    double h00 = T(l, l), h01 = T(l, l + 1), h10 = T(l + 1, l), h11 = T(l + 1, l + 1);
+    double x0 = fma(h00, h00, fma(h01, h10, fma(-ssum, h00, sprod)));
+    double x1 = h10 * (h00 + h11 - ssum);
+    double x2 = (nr == 3) ? h10 * T(l + 2, l + 1) : 0.0;
+    double v1, v2, tau, beta;
+    house3(nr, x0, x1, x2, v1, v2, tau, beta);
+    sh->r[0] = v1;
+    sh->r[1] = v2;
+    sh->r[2] = tau;
+  }
+  __syncthreads();
+  const int nu = U.p ? urows : 0;
   for (int k = l; k < i; ++k) {
-    int nr = min(3, i - k + 1);
-    if (cta_tid() == 0) {
-      double x0, x1, x2 = 0.0;
-      if (k == l) {
-        double h00 = T(l, l), h01 = T(l, l + 1), h10 = T(l + 1, l), h11 = T(l + 1, l + 1);
-        x0 = fma(h00, h00, fma(h01, h10, fma(-ssum, h00, sprod)));
-        x1 = h10 * (h00 + h11 - ssum);
-        if (nr == 3) x2 = h10 * T(l + 2, l + 1);
-      } else {
-        x0 = T(k, k - 1);
-        x1 = T(k + 1, k - 1);
-        if (nr == 3) x2 = T(k + 2, k - 1);
+    const int nr = min(3, i - k + 1);
+    const int slot = ((k - l) & 1) * 4;
+    const double v1 = sh->r[slot], v2 = sh->r[slot + 1], tau = sh->r[slot + 2];
+    if (tid < 32) {
+      if (tau != 0.0) {
+        const int cend = min(k + 2, m - 1);  // block columns k..cend (left product)
+        const int rend = min(k + 3, i);      // block rows k..rend (right product)
+        if (lane <= cend - k) refl3_apply(&T(k, k + lane), 1, nr, v1, v2, tau);
+        __syncwarp();
+        if (lane <= rend - k) refl3_apply(&T(k + lane, k), T.ld, nr, v1, v2, tau);
+        __syncwarp();
       }
-      double v1, v2, tau, beta;
-      house3(nr, x0, x1, x2, v1, v2, tau, beta);
-      if (k > l) {
-        T(k, k - 1) = beta;
-        T(k + 1, k - 1) = 0.0;
-        if (nr == 3) T(k + 2, k - 1) = 0.0;
+      if (lane == 0 && k + 1 < i) {
+        const int k1 = k + 1, nr1 = min(3, i - k1 + 1);
+        double x0 = T(k1, k), x1 = T(k1 + 1, k), x2 = (nr1 == 3) ? T(k1 + 2, k) : 0.0;
+        double w1, w2, t1, beta;
+        house3(nr1, x0, x1, x2, w1, w2, t1, beta);
+        T(k1, k) = beta;
+        T(k1 + 1, k) = 0.0;
+        if (nr1 == 3) T(k1 + 2, k) = 0.0;
+        const int s1 = 4 - slot;
+        sh->r[s1] = w1;
+        sh->r[s1 + 1] = w2;
+        sh->r[s1 + 2] = t1;
       }
-      sh->r[0] = v1;
-      sh->r[1] = v2;
-      sh->r[2] = tau;
-    }
-    __syncthreads();
-    double v1 = sh->r[0], v2 = sh->r[1], tau = sh->r[2];
-    if (tau != 0.0) {
-      for (int j = k + cta_tid(); j < m; j += cta_nt()) {
-        double* col = &T(k, j);
-        double a0 = col[0], a1 = col[1], a2 = (nr == 3) ? col[2] : 0.0;
-        double s = tau * fma(v2, a2, fma(v1, a1, a0));
-        col[0] = a0 - s;
-        col[1] = fma(-s, v1, a1);
-        if (nr == 3) col[2] = fma(-s, v2, a2);
-      }
-      __syncthreads();
-      const int nrr = min(k + 3, i) + 1;   // rows 0..min(k+3, i) of T
-      const int nu = U.p ? urows : 0;
-      for (int it = cta_tid(); it < nrr + nu; it += cta_nt()) {
-        const Mat& M = (it < nrr) ? T : U;
-        int r = (it < nrr) ? it : it - nrr;
-        double* c0 = &M(r, k);
-        double a0 = c0[0], a1 = c0[M.ld], a2 = (nr == 3) ? c0[2 * M.ld] : 0.0;
-        double s = tau * fma(v2, a2, fma(v1, a1, a0));
-        c0[0] = a0 - s;
-        c0[M.ld] = fma(-s, v1, a1);
-        if (nr == 3) c0[2 * M.ld] = fma(-s, v2, a2);
+    } else if (tau != 0.0) {
+      // items: rows of U first (global memory, the longest loads), then rows
+      // 0..k-1 of T, then columns k+3..m-1 of T; each thread loads both of
+      // its items of a round before computing either
+      const int c0 = k + 3;
+      const int nB = max(0, m - c0);
+      const int total = nu + k + nB;
+      const int bt = tid - 32, bn = nt - 32;
+      for (int base = 0; base < total; base += 2 * bn) {
+        double* p[2];
+        long long sd[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int it = base + bt + h * bn;
+          if (it < nu) {
+            p[h] = &U(it, k);
+            sd[h] = U.ld;
+          } else if (it < nu + k) {
+            p[h] = &T(it - nu, k);
+            sd[h] = T.ld;
+          } else if (it < total) {
+            p[h] = &T(k, c0 + (it - nu - k));
+            sd[h] = 1;
+          } else {
+            p[h] = nullptr;
+            sd[h] = 0;
+          }
+        }
+        double a[2][3];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          if (p[h]) {
+            a[h][0] = p[h][0];
+            a[h][1] = p[h][sd[h]];
+            a[h][2] = (nr == 3) ? p[h][2 * sd[h]] : 0.0;
+          }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          if (p[h]) {
+            double s = tau * fma(v2, a[h][2], fma(v1, a[h][1], a[h][0]));
+            p[h][0] = a[h][0] - s;
+            p[h][sd[h]] = fma(-s, v1, a[h][1]);
+            if (nr == 3) p[h][2 * sd[h]] = fma(-s, v2, a[h][2]);
+          }
       }
     }
     __syncthreads();

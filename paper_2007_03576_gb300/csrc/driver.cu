@@ -626,7 +626,7 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
     double* ubase = use_arena ? arena_alloc(need) : Lv.ubuf;
     int tok = timer.begin(st, PH_CHASE);
     ++g_stats.kernel_launches;
-    k_chase<<<na, CTA_THREADS, smem, st>>>(M.H, M.ldh, dpairs, ubase, a);
+    k_chase<<<na, CHASE_THREADS, smem, st>>>(M.H, M.ldh, dpairs, ubase, a);
     ck(cudaGetLastError());
     timer.end(st, tok);
     g_stats.window_launches += 1;

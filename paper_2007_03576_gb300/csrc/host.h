@@ -8,7 +8,6 @@
 #include "../../include/schur_gb300.h"
 #include "common.cuh"
 
-#define KWIN_MAX 112   // largest bulge-chase window (window + U in shared memory: 2 (k+1) k doubles)
 
 #include <array>
 #include <deque>

@@ -199,11 +199,92 @@ size_t chase_smem_bytes(int kwin) {
   return 2 * ld * (size_t)kwin * sizeof(double);
 }
 
-__global__ void __launch_bounds__(CTA_THREADS) k_chase(double* H, long long ldh, const double* pairs, double* Ubuf,
+#define CHASE_G 2
+
+// One product phase of k_chase over all bulges: SIDE 0 the left products
+// (rows kl..kl+2 of the window, columns kl..L-1), SIDE 1 the right products
+// (columns kl..kl+2 of window rows 0..min(kl+3, hil) and of U rows
+// ulo..uhi, the rows where U's columns kl..kl+2 can be nonzero).  Warp w
+// takes bulges w, w + nwarps, ...; its lanes run over the concatenated items
+// of those bulges, CHASE_G per thread with all loads issued before the
+// arithmetic.
+template <int SIDE>
+__device__ __forceinline__ void chase_phase(const Mat& W, const Mat& Us, int L, int ld, int nb, int hil,
+                                            const double* rv1, const double* rv2, const double* rtau,
+                                            const int* rk, const int* rnr, const int* rulo, const int* ruhi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  int end[4], kls[4], jj[4], nws[4];
+  int nmy = 0, tot = 0;
+  for (int j = warp; j < nb && nmy < 4; j += nwarps) {
+    if (rnr[j] == 0 || rtau[j] == 0.0) continue;
+    const int kl = rk[j];
+    const int nwr = (SIDE == 0) ? 0 : min(kl + 3, hil) + 1;
+    tot += (SIDE == 0) ? (L - kl) : (nwr + ruhi[j] - rulo[j] + 1);
+    end[nmy] = tot;
+    kls[nmy] = kl;
+    jj[nmy] = j;
+    nws[nmy] = nwr;
+    ++nmy;
+  }
+  for (int base = lane; base < tot; base += CHASE_G * 32) {
+    double* p[CHASE_G];
+    long long sd[CHASE_G];
+    int ms[CHASE_G];
+#pragma unroll
+    for (int g = 0; g < CHASE_G; ++g) {
+      const int it = base + g * 32;
+      p[g] = nullptr;
+      sd[g] = 0;
+      ms[g] = 0;
+      if (it >= tot) continue;
+      int m = 0;
+      while (it >= end[m]) ++m;
+      const int q = it - (m ? end[m - 1] : 0);
+      const int kl = kls[m];
+      if (SIDE == 0) {
+        p[g] = &W(kl, kl + q);
+        sd[g] = 1;
+      } else if (q < nws[m]) {
+        p[g] = &W(q, kl);
+        sd[g] = ld;
+      } else {
+        p[g] = &Us(q - nws[m] + rulo[jj[m]], kl);
+        sd[g] = ld;
+      }
+      ms[g] = m;
+    }
+    double a[CHASE_G][3];
+#pragma unroll
+    for (int g = 0; g < CHASE_G; ++g)
+      if (p[g]) {
+        const int nr = rnr[jj[ms[g]]];
+        a[g][0] = p[g][0];
+        a[g][1] = p[g][sd[g]];
+        a[g][2] = (nr == 3) ? p[g][2 * sd[g]] : 0.0;
+      }
+#pragma unroll
+    for (int g = 0; g < CHASE_G; ++g)
+      if (p[g]) {
+        const int j = jj[ms[g]];
+        const int nr = rnr[j];
+        const double v1 = rv1[j], v2 = rv2[j], t = rtau[j];
+        double s = t * (a[g][0] + v1 * a[g][1] + v2 * a[g][2]);
+        p[g][0] = a[g][0] - s;
+        p[g][sd[g]] = a[g][1] - s * v1;
+        if (nr == 3) p[g][2 * sd[g]] = a[g][2] - s * v2;
+      }
+  }
+}
+
+__global__ void __launch_bounds__(CHASE_THREADS) k_chase(double* H, long long ldh, const double* pairs, double* Ubuf,
                                                        const __grid_constant__ ChaseArgs args) {
   extern __shared__ double smem[];
   __shared__ double rv1[MAX_BULGES_PER_CHAIN], rv2[MAX_BULGES_PER_CHAIN], rtau[MAX_BULGES_PER_CHAIN];
   __shared__ int rk[MAX_BULGES_PER_CHAIN], rnr[MAX_BULGES_PER_CHAIN];
+  // rows ulo[c]..uhi[c] hold U's nonzeros in column c (U starts as I; a
+  // reflector on columns kl..kl+2 merges their ranges)
+  __shared__ short ulo[KWIN_MAX], uhi[KWIN_MAX];
+  __shared__ int rulo[MAX_BULGES_PER_CHAIN], ruhi[MAX_BULGES_PER_CHAIN];
   const ChainDesc& d = args.c[blockIdx.x];
   const int ws = d.ws;
   const int L = d.we - d.ws + 1;
@@ -217,6 +298,10 @@ __global__ void __launch_bounds__(CTA_THREADS) k_chase(double* H, long long ldh,
       W(i, j) = H[(ws + i) + (long long)(ws + j) * ldh];
       Us(i, j) = (i == j) ? 1.0 : 0.0;
     }
+  for (int c = tid; c < L; c += nt) {
+    ulo[c] = (short)c;
+    uhi[c] = (short)c;
+  }
   __syncthreads();
   const int nb = d.nb;
   const int hil = hi - ws;  // local index of hi
@@ -252,69 +337,30 @@ __global__ void __launch_bounds__(CTA_THREADS) k_chase(double* H, long long ldh,
         rtau[j] = t;
         rk[j] = kl;
         rnr[j] = nr;
+        int a0 = ulo[kl], b0 = uhi[kl];
+        for (int t2 = 1; t2 < nr; ++t2) {
+          a0 = min(a0, (int)ulo[kl + t2]);
+          b0 = max(b0, (int)uhi[kl + t2]);
+        }
+        for (int t2 = 0; t2 < nr; ++t2) {
+          ulo[kl + t2] = (short)a0;
+          uhi[kl + t2] = (short)b0;
+        }
+        rulo[j] = a0;
+        ruhi[j] = b0;
       } else {
         rnr[j] = 0;
       }
     }
     __syncthreads();
-    // (B) left products: bulge j on rows kl..kl+nr-1, in-window columns kl..L-1
-    {
-      int base = 0;
-      for (int j = 0; j < nb; ++j) {
-        int nr = rnr[j];
-        if (nr == 0) continue;
-        int kl = rk[j];
-        int cnt = L - kl;
-        double v1 = rv1[j], v2 = rv2[j], t = rtau[j];
-        int start = (tid - base) % nt;
-        if (start < 0) start += nt;
-        for (int c = start; c < cnt; c += nt) {
-          double* col = &W(kl, kl + c);
-          double a0 = col[0], a1 = col[1], a2 = (nr == 3) ? col[2] : 0.0;
-          double s = t * (a0 + v1 * a1 + v2 * a2);
-          col[0] = a0 - s;
-          col[1] = a1 - s * v1;
-          if (nr == 3) col[2] = a2 - s * v2;
-        }
-        base += cnt;
-      }
-    }
+    // (B) left products: slot -> (bulge j, window column c), active for
+    // c >= kl_j; (C) right products: slot -> (bulge j, row q), q < L a window
+    // row (active for q <= min(kl_j + 3, hil)), q >= L row q - L of U.
+    // Consecutive threads take consecutive columns / rows of one bulge; each
+    // thread loads the operands of CHASE_G slots before computing any.
+    chase_phase<0>(W, Us, L, ld, nb, hil, rv1, rv2, rtau, rk, rnr, rulo, ruhi);
     __syncthreads();
-    // (C) right products: bulge j on columns kl..kl+nr-1, window rows
-    // 0..min(kl+3, hil), and on all L rows of U
-    {
-      int base = 0;
-      for (int j = 0; j < nb; ++j) {
-        int nr = rnr[j];
-        if (nr == 0) continue;
-        int kl = rk[j];
-        double v1 = rv1[j], v2 = rv2[j], t = rtau[j];
-        int rmax = min(kl + 3, hil);
-        int cnt = rmax + 1;
-        int start = (tid - base) % nt;
-        if (start < 0) start += nt;
-        double* c0 = &W(0, kl);
-        for (int r = start; r < cnt; r += nt) {
-          double a0 = c0[r], a1 = c0[r + ld], a2 = (nr == 3) ? c0[r + 2 * ld] : 0.0;
-          double s = t * (a0 + v1 * a1 + v2 * a2);
-          c0[r] = a0 - s;
-          c0[r + ld] = a1 - s * v1;
-          if (nr == 3) c0[r + 2 * ld] = a2 - s * v2;
-        }
-        base += cnt;
-        start = (tid - base) % nt;
-        if (start < 0) start += nt;
-        double* u0 = &Us(0, kl);
-        for (int r = start; r < L; r += nt) {
-          double a0 = u0[r], a1 = u0[r + ld], a2 = (nr == 3) ? u0[r + 2 * ld] : 0.0;
-          double s = t * (a0 + v1 * a1 + v2 * a2);
-          u0[r] = a0 - s;
-          u0[r + ld] = a1 - s * v1;
-          if (nr == 3) u0[r + 2 * ld] = a2 - s * v2;
-        }
-        base += L;
-      }
-    }
+    chase_phase<1>(W, Us, L, ld, nb, hil, rv1, rv2, rtau, rk, rnr, rulo, ruhi);
     __syncthreads();
   }
   double* Uout = Ubuf + d.uoff;
