@@ -265,7 +265,7 @@ __device__ int cta_schur_one(const Mat& H, int n, const Mat& Z, const BatchedPar
   return (kbot >= 0) ? kbot + 1 : 0;
 }
 
-__global__ void __launch_bounds__(CTA_THREADS) k_batched(const BatchedDesc* __restrict__ desc,
+__global__ void __launch_bounds__(CTA_THREADS, 3) k_batched(const BatchedDesc* __restrict__ desc,
                                                          const int* __restrict__ order, int batch, int* counter,
                                                          int* info, BatchedScratch* scratch, BatchedParams P) {
   extern __shared__ double smem[];
