@@ -398,6 +398,25 @@ size_t apply_u_smem_bytes(int tn, int maxL) {
   return ((size_t)maxL * ldv + kc * ((size_t)maxL + 1)) * sizeof(double);
 }
 
+// One k of the register tile: the thread's CN vector entries of row k of X
+// are loaded once and multiplied into every active row block a.
+template <int CN>
+__device__ __forceinline__ void apply_u_k_impl(const double* sX, const double* sU, int krow, int kk, int LDV, int LDU,
+                                               int vg, int rg, int RG, int L, unsigned act, double (&acc)[8][CN]) {
+  const double* xr = sX + (size_t)krow * LDV + vg * CN;
+  double x[CN];
+#pragma unroll
+  for (int c = 0; c < CN; ++c) x[c] = xr[c];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    if (act & (1u << a)) {
+      const int i = rg + RG * a;
+      const double u = (i < L) ? sU[(size_t)kk * LDU + i] : 0.0;
+#pragma unroll
+      for (int c = 0; c < CN; ++c) acc[a][c] = fma(u, x[c], acc[a][c]);
+    }
+  }
+}
 template <int TN>
 __global__ void __launch_bounds__(CTA_THREADS) k_apply_u(const __grid_constant__ UpdArgs args) {
   extern __shared__ double smem[];
@@ -455,20 +474,18 @@ __global__ void __launch_bounds__(CTA_THREADS) k_apply_u(const __grid_constant__
         const int kg0 = kc + k16;
         const int kend = min(kn, k16 + 16);
         const int kg1 = kc + kend - 1;
+        // row blocks with a nonzero of U in this k block (uniform over the
+        // block: the test depends on a, not on the thread)
+        unsigned act = 0;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          if (a < RM) {
-            const bool skip = (kg0 - (RG * a + RG - 1) > t.lbw) || (RG * a - kg1 > t.ubw);
-            if (!skip) {
-              const int i = rg + RG * a;
-              for (int kk = k16; kk < kend; ++kk) {
-                const double* xr = sX + (size_t)(kc + kk) * LDV + vg * CN;
-                double u = (i < L) ? sU[(size_t)kk * LDU + i] : 0.0;
-#pragma unroll
-                for (int c = 0; c < CN; ++c) acc[a][c] = fma(u, xr[c], acc[a][c]);
-              }
-            }
-          }
+        for (int a = 0; a < 8; ++a)
+          if (a < RM && !((kg0 - (RG * a + RG - 1) > t.lbw) || (RG * a - kg1 > t.ubw))) act |= 1u << a;
+        if (act == 0) continue;
+        if (kend - k16 == 16) {
+#pragma unroll 4
+          for (int kk = k16; kk < k16 + 16; ++kk) apply_u_k_impl<CN>(sX, sU, kc + kk, kk, LDV, LDU, vg, rg, RG, L, act, acc);
+        } else {
+          for (int kk = k16; kk < kend; ++kk) apply_u_k_impl<CN>(sX, sU, kc + kk, kk, LDV, LDU, vg, rg, RG, L, act, acc);
         }
       }
     }
