@@ -117,6 +117,14 @@ def cpu_baseline_sample(n_sample=160, seed=2023):
     return json.loads(r.stdout.strip().splitlines()[-1])["sec"]
 
 
+def bench_config(args, world=1):
+    """The workload description shared by both arms of the bench."""
+    n = args.n
+    return {"workload": f"hess_n n={n} (Sec. 5.3) Hessenberg -> real Schur, Z accumulated, seed {args.seed}",
+            "n": n, "n_shifts": args.ns, "aed_window": args.nw, "deflation": "lapack-style",
+            "l2": "inputs larger than L2 (3.2 GB per matrix), no flush", "parallelism": f"replicas x{world}"}
+
+
 def reference_arm(args):
     """--impl reference: the CPU oracle as it stands, each step one bounded
     sample (order 160 hess_n reduction), scaled cubically to n."""
@@ -136,7 +144,7 @@ def reference_arm(args):
         "impl": "reference", "metric": f"n={args.n} FP64 Schur time", "value": value, "unit": "s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"hess_n n={args.n} Hessenberg -> real Schur, Z accumulated", "n": args.n},
+        "config": bench_config(args, args.gpus),
         "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -387,9 +395,7 @@ def main():
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"hess_n n={n} (Sec. 5.3) Hessenberg -> real Schur, Z accumulated, seed {args.seed}",
-                   "n": n, "n_shifts": args.ns, "aed_window": args.nw, "deflation": "lapack-style",
-                   "l2": "inputs larger than L2 (3.2 GB per matrix), no flush", "parallelism": f"replicas x{world}"},
+        "config": bench_config(args, world),
         "roofline": {"bound": "alu", "kernel": "k_apply_u (off-window products, FP64 FFMA)",
                      "achieved": achieved, "peak": FP64_PEAK_DERIVED, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_DERIVED) if achieved else None, "traffic": None,

@@ -399,14 +399,16 @@ size_t apply_u_smem_bytes(int tn, int maxL) {
 }
 
 // One k of the register tile: the thread's CN vector entries of row k of X
-// are loaded once and multiplied into every active row block a.
-template <int CN>
+// (vectors vg, vg + VG, vg + 2 VG, ...: consecutive lanes read consecutive
+// words, no bank conflicts) are loaded once and multiplied into every active
+// row block a.
+template <int CN, int VG>
 __device__ __forceinline__ void apply_u_k_impl(const double* sX, const double* sU, int krow, int kk, int LDV, int LDU,
                                                int vg, int rg, int RG, int L, unsigned act, double (&acc)[8][CN]) {
-  const double* xr = sX + (size_t)krow * LDV + vg * CN;
+  const double* xr = sX + (size_t)krow * LDV + vg;
   double x[CN];
 #pragma unroll
-  for (int c = 0; c < CN; ++c) x[c] = xr[c];
+  for (int c = 0; c < CN; ++c) x[c] = xr[c * VG];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     if (act & (1u << a)) {
@@ -483,9 +485,9 @@ __global__ void __launch_bounds__(CTA_THREADS) k_apply_u(const __grid_constant__
         if (act == 0) continue;
         if (kend - k16 == 16) {
 #pragma unroll 4
-          for (int kk = k16; kk < k16 + 16; ++kk) apply_u_k_impl<CN>(sX, sU, kc + kk, kk, LDV, LDU, vg, rg, RG, L, act, acc);
+          for (int kk = k16; kk < k16 + 16; ++kk) apply_u_k_impl<CN, VG>(sX, sU, kc + kk, kk, LDV, LDU, vg, rg, RG, L, act, acc);
         } else {
-          for (int kk = k16; kk < kend; ++kk) apply_u_k_impl<CN>(sX, sU, kc + kk, kk, LDV, LDU, vg, rg, RG, L, act, acc);
+          for (int kk = k16; kk < kend; ++kk) apply_u_k_impl<CN, VG>(sX, sU, kc + kk, kk, LDV, LDU, vg, rg, RG, L, act, acc);
         }
       }
     }
@@ -497,7 +499,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_apply_u(const __grid_constant__
         int i = rg + RG * a;
         if (i < L) {
 #pragma unroll
-          for (int c = 0; c < CN; ++c) sX[i * LDV + vg * CN + c] = acc[a][c];
+          for (int c = 0; c < CN; ++c) sX[i * LDV + vg + VG * c] = acc[a][c];
         }
       }
     }
