@@ -387,8 +387,13 @@ int apply_u_tn(int maxL) {
   return 8;
 }
 
+// Rows of U staged per chunk: at most half of L (rounded up to 16), so that
+// the chase windows' products (L <= 112, 64 vectors) take ~87 KB of shared
+// memory and two blocks share an SM, and at most 16384 / (L + 1) in general.
 __host__ __device__ static inline int apply_u_kc(int L) {
   int kc = 16384 / (L + 1);
+  int half = ((L + 1) / 2 + 15) / 16 * 16;
+  if (kc > half) kc = half;
   return kc < L ? (kc < 1 ? 1 : kc) : L;
 }
 
