@@ -92,7 +92,7 @@ typedef struct {
   int chase_launches;       /* bulge-chase launches at the top level */
   /* device time per phase in ms (opts->timing = 1 only): */
   double t_chase_ms;        /* bulge-chase windows of the sweeps */
-  double t_update_ms;       /* off-window products of the sweeps */
+  double t_update_ms;       /* off-window products of the sweeps on H (main and side streams) */
   double t_aed_ms;          /* AED: window Schur form, deflation, reordering */
   double t_aed_update_ms;   /* off-window products of AED */
   double t_small_ms;        /* double-shift QR of small blocks (+ products) */
@@ -102,7 +102,7 @@ typedef struct {
   double aed_cycles_schur;
   double aed_cycles_post;
   long long kernel_launches; /* kernels launched by the call (all levels) */
-  double t_z_ms;            /* products applied to Z on the second stream (overlaps the rest) */
+  double t_z_ms;            /* products applied to Z on the Z stream (overlaps the rest) */
 } schur_stats;
 
 /* Fill *opts with the defaults listed above. Returns SCHUR_OK. */
@@ -130,6 +130,19 @@ int schur_workspace_size(int n, const schur_opts* opts, size_t* bytes);
  *          the positive imaginary part first (the order of S's diagonal)
  *                                                                    (args 6, 7)
  *   opts   may be NULL (defaults)                                   (arg 8)
+ * Streams: the call creates three streams of its own and joins them to
+ * opts->stream by events (its first kernel waits for the work already on
+ * opts->stream; opts->stream waits for its last one).  The main stream has
+ * the greatest priority and carries the scan, the AED and the chase; a side
+ * stream one level lower carries each chase step's products on the rows
+ * above its windows; a least-priority stream carries every product on Z
+ * (Sec. 3.4: updates outside the critical path are delayed).  The call is
+ * therefore not capturable into a CUDA graph; schur_hessenberg_batched is.
+ * With the environment variable SCHUR_TRACE=<file> set (timing is then on
+ * whatever opts->timing says), every timed bracket of the call is written to
+ * <file> as CSV
+ * "stream,phase,start_ms,end_ms" (streams 0 main, 1 Z, 2 side; phases as in
+ * schur_stats: 0 chase, 1 products, 2 AED, 3 AED products, 4 small QR, 5 Z).
  */
 int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, double* wr, double* wi,
                      const schur_opts* opts);

@@ -66,3 +66,65 @@ def test_chase_transform_band(n, npairs, nbc):
         r, c = np.nonzero(P)
         assert np.max(r - c) <= 2 + 2 * min(nb - 1, delta - 1)
         assert np.max(c - r) <= delta + 1
+
+
+def range_rule(lo, hi, ws, we, tau0, tau1, nb):
+    """The chase kernel's bookkeeping of U's nonzero rows: column c's rows lie
+    in [ulo[c], uhi[c]], initially [c, c]; a reflector on columns kl..kl+nr-1
+    gives all of them the union of their ranges.  Yields, before each step's
+    right products, the ranges next to the structural pattern of U."""
+    L = we - ws + 1
+    ulo, uhi = np.arange(L), np.arange(L)
+    P = np.eye(L, dtype=bool)
+    for tau in range(tau0, tau1):
+        for j in range(nb):
+            k = lo + tau - 3 * j
+            if lo <= k <= hi - 1:
+                nr = min(3, hi - k + 1)
+                kl = k - ws
+                cols = np.arange(kl, kl + nr)
+                a, b = ulo[cols].min(), uhi[cols].max()
+                ulo[cols], uhi[cols] = a, b
+                rows = P[:, cols].any(axis=1)
+                P[np.ix_(rows, cols)] = True
+        yield ulo.copy(), uhi.copy(), P.copy()
+
+
+@pytest.mark.parametrize("n,npairs,nbc", [(300, 8, 4), (400, 30, 10), (260, 4, 1), (500, 64, 32), (700, 32, 16)])
+def test_chase_u_row_ranges_cover_nonzeros(n, npairs, nbc):
+    """The right products of the chase touch only rows ulo..uhi of U's
+    columns: after every step those ranges contain every structural nonzero,
+    and they are narrower than the window (the saving the kernel takes)."""
+    saved = total = 0
+    for ws, we, tau0, tau1, nb, delta in schedule(0, n - 1, npairs, nbc):
+        L = we - ws + 1
+        for ulo, uhi, P in range_rule(0, n - 1, ws, we, tau0, tau1, nb):
+            r, c = np.nonzero(P)
+            assert np.all(r >= ulo[c]) and np.all(r <= uhi[c])
+            saved += int(np.sum(L - (uhi - ulo + 1)))
+            total += L * L
+    assert saved > 0.2 * total
+
+
+def test_chase_u_row_ranges_numeric():
+    """The same with numbers: U accumulated from random 3x3 reflectors of one
+    window schedule has no nonzero outside the tracked ranges."""
+    rng = np.random.default_rng(5)
+    for ws, we, tau0, tau1, nb, delta in schedule(0, 299, 16, 8):
+        L = we - ws + 1
+        U = np.eye(L)
+        ulo, uhi = np.arange(L), np.arange(L)
+        for tau in range(tau0, tau1):
+            for j in range(nb):
+                k = tau - 3 * j
+                if 0 <= k <= 298:
+                    nr = min(3, 299 - k + 1)
+                    kl = k - ws
+                    cols = np.arange(kl, kl + nr)
+                    a, b = ulo[cols].min(), uhi[cols].max()
+                    ulo[cols], uhi[cols] = a, b
+                    v = rng.standard_normal(nr)
+                    Pm = np.eye(nr) - 2.0 * np.outer(v, v) / (v @ v)
+                    U[:, cols] = U[:, cols] @ Pm
+        r, c = np.nonzero(U)
+        assert np.all(r >= ulo[c]) and np.all(r <= uhi[c])
