@@ -18,8 +18,8 @@ Conventions
 * A shift pair is stored as (sum, product) = (s1 + s2, s1 * s2); for a
   complex conjugate pair both are real.
 
-Where the paper is silent the reading taken is stated at the function and
-collected in DESIGN.md (section "Readings of the paper").
+Where the paper is silent the reading taken is stated at the function that
+applies it.
 """
 
 import math
