@@ -128,3 +128,60 @@ def test_chase_u_row_ranges_numeric():
                     U[:, cols] = U[:, cols] @ Pm
         r, c = np.nonzero(U)
         assert np.all(r >= ulo[c]) and np.all(r <= uhi[c])
+
+
+def launches(lo, hi, npairs, nbc_req):
+    """The windows of each chase launch of a sweep: {launch: [(ws, we), ...]}
+    (same schedule as ``schedule``, grouped by launch)."""
+    nbc = max(1, min(nbc_req, npairs, MAX_BULGES))
+    nbc = max(nbc, (npairs + MAX_CHAINS - 1) // MAX_CHAINS)
+    kwin = min(KWIN_MAX, max(6 * nbc, 48))
+    delta = kwin - 3 * nbc - 1
+    if delta < 1:
+        kwin, delta = 3 * nbc + 2, 1
+    nchain = (npairs + nbc - 1) // nbc
+    S = (kwin + delta + 3 * nbc + 2 + delta - 1) // delta
+    nbs = [min(nbc, npairs - c * nbc) for c in range(nchain)]
+    tend = [(hi - lo - 1) + 3 * (nbs[c] - 1) for c in range(nchain)]
+    last = max(c * S + (tend[c] + delta) // delta for c in range(nchain))
+    out = []
+    for s in range(last):
+        wins = []
+        for c in range(nchain):
+            if s < c * S:
+                continue
+            tau0 = (s - c * S) * delta
+            if tau0 > tend[c]:
+                continue
+            tau1 = min(tau0 + delta, tend[c] + 1)
+            kmin, kmax = max(lo, lo + tau0 - 3 * (nbs[c] - 1)), min(hi - 1, lo + tau1 - 1)
+            if kmin > kmax:
+                continue
+            wins.append((lo if kmin == lo else kmin - 1, min(kmax + 3, hi)))
+        out.append(wins)
+    return out
+
+
+@pytest.mark.parametrize("n,npairs,nbc,lo", [(20000, 64, 16, 0), (5000, 32, 16, 37), (3000, 32, 8, 0),
+                                              (2000, 64, 4, 11), (700, 10, 3, 0), (20000, 128, 32, 5)])
+def test_right_products_miss_the_next_chase_step(n, npairs, nbc, lo):
+    """A chase step's right products (rows 0..ws-1 of columns ws..we of each
+    window) touch nothing the next chase step reads (its windows), so they run
+    beside it on another stream.  The next step's left products (rows of its
+    windows, columns to the right) do meet them where a following chain's rows
+    cross the columns of the chain ahead: that is why they wait."""
+    hi = n - 6
+    sch = launches(lo, hi, npairs, nbc)
+    meets_left = 0
+    for s in range(len(sch) - 1):
+        for ws, we in sch[s]:
+            for ws2, we2 in sch[s + 1]:
+                # right products of (ws, we) vs window (ws2, we2) of the next launch
+                rows_meet = ws2 < ws
+                cols_meet = not (we2 < ws or ws2 > we)
+                assert not (rows_meet and cols_meet)
+                # left products of (ws2, we2): rows ws2..we2, columns > we2
+                if ws2 < ws and we2 < we:
+                    meets_left += 1
+    if npairs > nbc:
+        assert meets_left > 0
