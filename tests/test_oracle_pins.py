@@ -461,3 +461,38 @@ def test_syn_base_spectrum_golden():
             assert l.real in base
     assert np.sum(lam.imag > 0) == 2 and np.sum(lam.imag < 0) == 2
     assert set(x for x in reals) <= set(base)
+
+
+def test_eig_condition_closed_forms():
+    """Eigenvalue condition numbers (the kappa_i that scale every eigenvalue
+    tolerance): 1 for every eigenvalue of a normal quasi-triangular matrix
+    (diagonal reals and standardised 2x2 blocks [[a, b], [-b, a]]), and
+    sqrt(1 + b^2 / (a - c)^2) for both eigenvalues of [[a, b], [0, c]]
+    (x = e_1, y proportional to (1, b / (a - c)) for lambda = a)."""
+    S = np.zeros((7, 7))
+    S[0, 0] = 3.0
+    S[1:3, 1:3] = [[1.0, 2.0], [-2.0, 1.0]]
+    S[3, 3] = -4.0
+    S[4:6, 4:6] = [[-0.5, 0.25], [-0.25, -0.5]]
+    S[6, 6] = 7.0
+    lam, kap = metrics.eig_condition(S)
+    assert np.allclose(kap, 1.0, atol=1e-12)
+    for a, b, c in [(1.0, 5.0, 3.0), (2.0, -0.01, -1.0), (0.0, 100.0, 1e-3)]:
+        T = np.array([[a, b], [0.0, c]])
+        lam, kap = metrics.eig_condition(T)
+        expect = np.sqrt(1.0 + b * b / (a - c) ** 2)
+        assert np.allclose(kap, expect, rtol=1e-12), (kap, expect)
+
+
+def test_match_eigenvalues_recovers_permutation():
+    """The optimal one-to-one matching used by every eigenvalue comparison
+    recovers a known permutation under perturbations smaller than half the
+    gap, and reports the perturbation sizes."""
+    rng = np.random.default_rng(3)
+    a = np.arange(40) * 1.0 + 1j * (np.arange(40) % 3)
+    perm = rng.permutation(40)
+    noise = 1e-3 * (rng.standard_normal(40) + 1j * rng.standard_normal(40))
+    b = a[perm] + noise
+    p, dist = metrics.match_eigenvalues(a, b)
+    assert np.array_equal(b[p], b[np.argsort(perm)])
+    assert np.allclose(np.sort(dist), np.sort(np.abs(noise)))
