@@ -189,11 +189,13 @@ const char* schur_last_error_detail(void);
  *   batch        number of matrices, >= 0                            (arg 1)
  *   n            host array [batch]: orders, 1 <= n[b] <= 1024          (arg 2)
  *   H            host array [batch] of device pointers (as in schur_hessenberg)
- *   ldh          host array [batch]
+ *                                                                     (arg 3)
+ *   ldh          host array [batch], ldh[b] >= n[b]                   (arg 4)
  *   Z            host array [batch] of device pointers (always accumulated;
  *                opts->z_init applies)                               (arg 5)
- *   ldz          host array [batch]
+ *   ldz          host array [batch], ldz[b] >= n[b]                   (arg 6)
  *   wr, wi       host arrays [batch] of device pointers, length n[b] each
+ *                                                                (args 7, 8)
  *   info         host array [batch] (output): per-matrix status as in
  *                schur_hessenberg                                     (arg 9)
  *   opts         may be NULL                                          (arg 10)
@@ -221,11 +223,13 @@ int schur_batched_set_table(int nbuckets, const int* max_n, const int* ns, const
  * x_k, y_k the right / left eigenvectors of S (first-order eigenvalue
  * perturbation: d lambda = y^H dH x / y^H x).  The eigenvectors come from
  * block back / forward substitution on the quasi-triangular S.
- *   n          order                                                (arg 1)
+ *   n          order, 0 <= n <= 1024                                (arg 1)
  *   S, lds     device, the standardised Schur factor from schur_hessenberg
+ *                                                                (args 2, 3)
  *   Z, ldz     device, the Schur vectors from schur_hessenberg       (args 4, 5)
  *   wr, wi     device, eigenvalues in S's order                      (args 6, 7)
  *   gwr, gwi   device, length n: cotangents of Re / Im of each eigenvalue
+ *                                                                (args 8, 9)
  *   dH, lddh   device, output n x n                                  (args 10, 11)
  *   opts       may be NULL (stream, workspace)                        (arg 12)
  */
@@ -234,7 +238,9 @@ int schur_eig_backward(int n, const double* S, int lds, const double* Z, int ldz
                        const schur_opts* opts);
 
 /* schur_eig_backward for `batch` matrices in one launch sequence; arrays as
- * in schur_hessenberg_batched (host arrays of device pointers). */
+ * in schur_hessenberg_batched (host arrays of device pointers; n, lds, ldz
+ * and lddh host arrays of ints).  A bad argument i returns -i, also when
+ * only one matrix's entry of that array is bad. */
 int schur_eig_backward_batched(int batch, const int* n, double* const* S, const int* lds, double* const* Z,
                                const int* ldz, double* const* wr, double* const* wi, double* const* gwr,
                                double* const* gwi, double* const* dH, const int* lddh,

@@ -529,19 +529,29 @@ extern "C" int schur_eig_backward_batched(int batch, const int* n, double* const
   if (batch < 0) return -1;
   if (batch == 0) return SCHUR_OK;
   if (!n) return -2;
-  if (!S || !lds) return -3;
-  if (!Z || !ldz) return -5;
+  if (!S) return -3;
+  if (!lds) return -4;
+  if (!Z) return -5;
+  if (!ldz) return -6;
   if (!wr) return -7;
   if (!wi) return -8;
   if (!gwr) return -9;
   if (!gwi) return -10;
-  if (!dH || !lddh) return -11;
+  if (!dH) return -11;
+  if (!lddh) return -12;
   std::vector<AdjMatrix> ms(batch);
   for (int b = 0; b < batch; ++b) {
     if (n[b] < 1 || n[b] > ADJ_NMAX) return -2;
-    if (!S[b] || lds[b] < n[b]) return -3;
-    if (!Z[b] || ldz[b] < n[b]) return -5;
-    if (!dH[b] || lddh[b] < n[b]) return -11;
+    if (!S[b]) return -3;
+    if (lds[b] < n[b]) return -4;
+    if (!Z[b]) return -5;
+    if (ldz[b] < n[b]) return -6;
+    if (!wr[b]) return -7;
+    if (!wi[b]) return -8;
+    if (!gwr[b]) return -9;
+    if (!gwi[b]) return -10;
+    if (!dH[b]) return -11;
+    if (lddh[b] < n[b]) return -12;
     ms[b] = AdjMatrix{n[b], S[b], Z[b], wr[b], wi[b], gwr[b], gwi[b], dH[b], lds[b], ldz[b], lddh[b]};
   }
   return run_backward(ms, opts);

@@ -419,8 +419,10 @@ extern "C" int schur_hessenberg_batched(int batch, const int* n, double* const* 
   if (!info) return -9;
   for (int b = 0; b < batch; ++b) {
     if (n[b] < 1 || n[b] > 1024) return -2;
-    if (!H[b] || ldh[b] < n[b]) return -3;
-    if (!Z[b] || ldz[b] < n[b]) return -5;
+    if (!H[b]) return -3;
+    if (ldh[b] < n[b]) return -4;
+    if (!Z[b]) return -5;
+    if (ldz[b] < n[b]) return -6;
     if (!wr[b]) return -7;
     if (!wi[b]) return -8;
   }

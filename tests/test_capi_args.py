@@ -1,0 +1,135 @@
+"""Argument checks of every C-ABI entry point, on the host (no GPU).
+
+The header's convention: a bad argument i (1-based) returns -i, before any
+device work.  Each case starts from valid arguments and breaks one at a
+time.  Device pointers are dummies that a rejected call never touches; no
+call here has all of its arguments valid, so none reaches the device."""
+
+import ctypes
+
+import pytest
+
+from paper_2007_03576_gb300 import _lib
+
+DEV = ctypes.c_void_p(4096)  # stands for a device pointer; never dereferenced
+N = 8
+
+
+def _opts():
+    return ctypes.byref(_lib.make_opts(0))
+
+
+def _expect(fn, args, i, bad):
+    a = list(args)
+    a[i] = bad
+    rc = fn(*a)
+    assert rc == -(i + 1), (fn.__name__, i + 1, bad, rc)
+
+
+SCALAR_CASES = [
+    # name, valid arguments (opts appended), {0-based index: [bad values]}
+    ("schur_hessenberg", [N, DEV, N, DEV, N, DEV, DEV],
+     {0: [-1], 1: [None], 2: [N - 1, 0], 3: [None], 4: [N - 1], 5: [None], 6: [None]}),
+    ("schur_hessenberg_noalloc", [N, DEV, N, DEV, N, DEV, DEV],
+     {0: [-1], 1: [None], 2: [N - 1], 3: [None], 4: [N - 1], 5: [None], 6: [None]}),
+    ("schur_eig_backward", [N, DEV, N, DEV, N, DEV, DEV, DEV, DEV, DEV, N],
+     {0: [-1, 1025], 1: [None], 2: [N - 1], 3: [None], 4: [N - 1], 5: [None], 6: [None], 7: [None],
+      8: [None], 9: [None], 10: [N - 1]}),
+    ("schur_sweep", [N, DEV, N, DEV, N, 0, N - 1, (ctypes.c_double * 4)(), 2, 0],
+     {0: [0], 1: [None], 2: [N - 1], 4: [N - 1], 5: [-1, N], 6: [1, N], 7: [None], 8: [0, 32 * 32 + 1]}),
+    ("schur_aed", [N, DEV, N, DEV, N, 0, N - 1, 4, ctypes.byref(ctypes.c_int()), None, None, None],
+     {0: [0], 1: [None], 2: [N - 1], 4: [N - 1], 5: [-1, N], 6: [-1, N], 7: [0, N + 1], 8: [None]}),
+    ("schur_small_qr", [N, DEV, N, DEV, N, 0, N - 1],
+     {0: [0], 1: [None], 2: [N - 1], 4: [N - 1], 5: [-1, N], 6: [-1, N]}),
+    ("schur_apply_u", [0, DEV, N, 0, 0, N, 4, DEV, 4],
+     {0: [2, -1], 1: [None], 2: [0], 3: [-1], 4: [-1], 5: [-1], 6: [0, 1025], 7: [None], 8: [3]}),
+    ("schur_fastmath_eval", [N, DEV, DEV],
+     {0: [-1], 1: [None], 2: [None]}),
+]
+
+
+@pytest.mark.parametrize("name,args,bad", SCALAR_CASES, ids=[c[0] for c in SCALAR_CASES])
+def test_scalar_entry_points_reject_each_bad_argument(name, args, bad):
+    lib = _lib.load()
+    fn = getattr(lib, name)
+    full = list(args) + [_opts()]
+    for i, values in bad.items():
+        for v in values:
+            _expect(fn, full, i, v)
+
+
+def _host_arrays(batch, n):
+    ints = lambda v: (ctypes.c_int * batch)(*([v] * batch))
+    ptrs = lambda: (ctypes.c_void_p * batch)(*([4096] * batch))
+    return ints, ptrs
+
+
+def test_batched_rejects_each_bad_argument():
+    lib = _lib.load()
+    B = 3
+    ints, ptrs = _host_arrays(B, N)
+    info = (ctypes.c_int * B)()
+    valid = [B, ints(N), ptrs(), ints(N), ptrs(), ints(N), ptrs(), ptrs(), info, _opts()]
+    fn = lib.schur_hessenberg_batched
+    assert fn(0, None, None, None, None, None, None, None, None, _opts()) == 0
+    _expect(fn, valid, 0, -1)
+    for i in range(1, 9):  # a missing array
+        _expect(fn, valid, i, None)
+    # one bad entry in the middle of an array
+    bad_n = ints(N); bad_n[1] = 0
+    _expect(fn, valid, 1, bad_n)
+    bad_n = ints(N); bad_n[1] = 1025
+    _expect(fn, valid, 1, bad_n)
+    for i in (2, 4, 6, 7):  # a null device pointer for one matrix
+        p = ptrs(); p[2] = None
+        _expect(fn, valid, i, p)
+    for i in (3, 5):  # a leading dimension below n for one matrix
+        ld = ints(N); ld[1] = N - 1
+        _expect(fn, valid, i, ld)
+
+
+def test_batched_backward_rejects_each_bad_argument():
+    lib = _lib.load()
+    B = 3
+    ints, ptrs = _host_arrays(B, N)
+    valid = [B, ints(N), ptrs(), ints(N), ptrs(), ints(N), ptrs(), ptrs(), ptrs(), ptrs(), ptrs(), ints(N),
+             _opts()]
+    fn = lib.schur_eig_backward_batched
+    assert fn(0, *([None] * 11), _opts()) == 0
+    _expect(fn, valid, 0, -1)
+    for i in range(1, 12):
+        _expect(fn, valid, i, None)
+    bad_n = ints(N); bad_n[2] = 1025
+    _expect(fn, valid, 1, bad_n)
+    for i in (2, 4, 6, 7, 8, 9, 10):
+        p = ptrs(); p[1] = None
+        _expect(fn, valid, i, p)
+    for i in (3, 5, 11):
+        ld = ints(N); ld[0] = N - 1
+        _expect(fn, valid, i, ld)
+
+
+def test_set_table_rejects_bad_tables():
+    lib = _lib.load()
+    arr = lambda *v: (ctypes.c_int * len(v))(*v)
+    fn = lib.schur_batched_set_table
+    assert fn(9, arr(1), arr(8), arr(24)) == -1
+    assert fn(-1, arr(1), arr(8), arr(24)) == -1
+    assert fn(1, None, arr(8), arr(24)) == -2
+    assert fn(1, arr(100), None, arr(24)) == -3
+    assert fn(1, arr(100), arr(8), None) == -4
+    assert fn(1, arr(100), arr(8), arr(3)) == -4      # window below 4
+    assert fn(1, arr(100), arr(1), arr(24)) == -3     # fewer than 2 shifts
+    assert fn(0, None, None, None) == 0               # built-in table again
+
+
+def test_noalloc_order_limit_and_workspace_args():
+    lib = _lib.load()
+    fn = lib.schur_hessenberg_noalloc
+    assert fn(1025, DEV, 1025, DEV, 1025, DEV, DEV, _opts()) == _lib.SCHUR_ERR_TOO_LARGE
+    assert fn(0, None, 1, None, 1, None, None, _opts()) == 0
+    b = ctypes.c_size_t(0)
+    assert lib.schur_workspace_size(N, _opts(), None) == -3
+    assert lib.schur_workspace_size(N, None, ctypes.byref(b)) == 0 and b.value > 0
+    assert lib.schur_default_opts(None) == -1
+    assert lib.schur_last_stats(None) == -1
