@@ -97,7 +97,11 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline_sample(n_sample=160, seed=2023):
+# order of the CPU oracle sample: ~10 s of one-thread work on the hosts used
+CPU_SAMPLE_N = 400
+
+
+def cpu_baseline_sample(n_sample=CPU_SAMPLE_N, seed=2023):
     """Time the CPU oracle (one thread) on a bounded sample: one hess_n
     reduction of order n_sample, with the same shift/window rules."""
     code = (
@@ -127,11 +131,11 @@ def bench_config(args, world=1):
 
 def reference_arm(args):
     """--impl reference: the CPU oracle as it stands, each step one bounded
-    sample (order 160 hess_n reduction), scaled cubically to n."""
+    sample (one hess_n reduction of order CPU_SAMPLE_N), scaled cubically to n."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n_sample = 160
+    n_sample = CPU_SAMPLE_N
     for _ in range(args.warmup):
         cpu_baseline_sample(n_sample, args.seed)
     secs = [cpu_baseline_sample(n_sample, args.seed) for _ in range(args.steps)]
@@ -375,7 +379,7 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline:
-        n_sample = 160
+        n_sample = CPU_SAMPLE_N
         t = cpu_baseline_sample(n_sample, args.seed)
         cpu = {"value": t * (n / n_sample) ** 3, "unit": "s", "cores": 1, "kind": "oracle",
                "sample": f"oracle (numpy FP64, 1 thread) on one n={n_sample} hess_n reduction: {t:.2f} s, "
