@@ -7,8 +7,13 @@
 // (how many eigenvalues deflated, how many shift pairs are ready).  A sweep is
 // then issued without further synchronisation as a sequence of window steps:
 // one k_chase launch (one block per bulge chain, Sec. 2.4) followed by the
-// off-window products, H-left plus Z first, then H-right (the two overlap on
-// blocks H[window_i, window_j], where left and right products commute).
+// step's off-window products on three streams of the call (priorities as in
+// Sec. 3.4): the left products of H on the main stream, the right products on
+// the rows above the windows on a side stream, beside the next k_chase
+// launch, and the products on Z on a least-priority stream, released at the
+// end of the sweep so that they run beside the next AED.  Left and right
+// products meet on blocks H[window_i, window_j], where they commute but would
+// race; the next step's left products wait for the side stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
