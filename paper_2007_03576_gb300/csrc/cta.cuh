@@ -13,8 +13,6 @@
 
 struct CtaShared {
   double r[8];       // reflector / rotation broadcast
-  double q[16];      // 4x4 orthogonal factor of a swap
-  double d[16];      // new 4x4 diagonal block of a swap
   double red[32];    // block reductions
   int iv[8];         // integer broadcast
 };
