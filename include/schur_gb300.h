@@ -60,7 +60,10 @@ extern "C" {
 #define SCHUR_DEFLATION_FIXED 2  /* item 3, |entry| <= fixed_thold */
 
 typedef struct {
-  int struct_size;     /* sizeof(schur_opts); set by schur_default_opts */
+  int struct_size;     /* sizeof(schur_opts); set by schur_default_opts.
+                          Every entry point reads the first struct_size
+                          bytes over the defaults; struct_size <= 0 reads
+                          the whole struct of this header's layout */
   int n_shifts;        /* shifts per sweep (even); 0 = size table */
   int aed_window;      /* AED window nw; 0 = size table */
   int bulges_per_chain;/* bulges chased together in one window; 0 = auto */
@@ -159,9 +162,12 @@ int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, double* wr, 
  * rows), so it suits small and medium orders.
  *   - Allocates nothing: its scratch (about 37 KB) is a fixed array in
  *     device memory that every device holding the library keeps until the
- *     process exits.  The first call on a device looks up that array's
- *     device address (the device must be current); make that first call
- *     before any stream capture.
+ *     process exits.  The first call on a device sets the entry point up
+ *     there (the device must be current): it looks up that array's device
+ *     address and raises the shared-memory limits of the library's kernels
+ *     to the device maximum, once; make that first call before any stream
+ *     capture.  No call changes a kernel attribute afterwards, so calls of
+ *     the other entry points on other host threads are not affected.
  *   - n > 1024 returns SCHUR_ERR_TOO_LARGE without touching the device.
  *   - All calls share the one array: calls that may overlap on the GPU
  *     (different streams or host threads) race and must be serialised by

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/schur_gb300.h"
@@ -388,10 +389,30 @@ struct AdjMatrix {
 using schur::ck_at;
 using schur::CudaError;
 
+// k_adj_vectors' shared-memory limit is raised to the device maximum once per
+// device (never lowered), so that concurrent calls on other host threads never
+// see a limit below the size they launch with.
+static std::mutex g_adj_mu;
+static bool g_adj_done[64] = {false};
+
+static void adj_raise_limit() {
+  int dev = 0;
+  ck_at(cudaGetDevice(&dev), __LINE__);
+  if (dev < 0 || dev >= 64) throw CudaError{cudaErrorInvalidDevice};
+  std::lock_guard<std::mutex> lock(g_adj_mu);
+  if (g_adj_done[dev]) return;
+  int optin = 0;
+  ck_at(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), __LINE__);
+  cudaFuncAttributes fa;
+  ck_at(cudaFuncGetAttributes(&fa, k_adj_vectors), __LINE__);
+  ck_at(cudaFuncSetAttribute(k_adj_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes), __LINE__);
+  g_adj_done[dev] = true;
+}
+
 int run_backward(const std::vector<AdjMatrix>& ms, const schur_opts* opts) {
   schur_opts o;
-  schur_default_opts(&o);
-  if (opts) memcpy(&o, opts, std::min((size_t)std::max(opts->struct_size, 0), sizeof(o)));
+  schur::read_opts(opts, &o);
   cudaStream_t st = (cudaStream_t)o.stream;
   const int nb = (int)ms.size();
   size_t ws_doubles = 0;
@@ -409,6 +430,7 @@ int run_backward(const std::vector<AdjMatrix>& ms, const schur_opts* opts) {
   int rc = SCHUR_OK;
   try {
     schur::init_kernel_attributes();
+    adj_raise_limit();
     if (o.workspace && o.workspace_bytes >= need) {
       mem = (char*)o.workspace;
     } else if (o.workspace) {
@@ -434,7 +456,6 @@ int run_backward(const std::vector<AdjMatrix>& ms, const schur_opts* opts) {
     GemmTask* dtask = (GemmTask*)((char*)ddesc + desc_bytes);
     ck_at(cudaMemcpyAsync(ddesc, hd.data(), nb * sizeof(AdjDesc), cudaMemcpyHostToDevice, st), __LINE__);
     size_t smem = (size_t)ADJ_WARPS * 2 * nmax * sizeof(double);
-    ck_at(cudaFuncSetAttribute(k_adj_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), __LINE__);
     k_adj_vectors<<<(items + ADJ_WARPS - 1) / ADJ_WARPS, 32 * ADJ_WARPS, smem, st>>>(ddesc, nb, items, nmax);
     ck_at(cudaGetLastError(), __LINE__);
     ++schur::g_stats.kernel_launches;

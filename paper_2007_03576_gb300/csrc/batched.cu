@@ -427,8 +427,7 @@ extern "C" int schur_hessenberg_batched(int batch, const int* n, double* const* 
     if (!wi[b]) return -8;
   }
   schur_opts o;
-  schur_default_opts(&o);
-  if (opts) memcpy(&o, opts, std::min((size_t)std::max(opts->struct_size, 0), sizeof(o)));
+  read_opts(opts, &o);
   cudaStream_t st = (cudaStream_t)o.stream;
   BatchedParams P;
   if (g_bparams_set)
@@ -448,7 +447,6 @@ extern "C" int schur_hessenberg_batched(int batch, const int* n, double* const* 
     init_kernel_attributes();
     size_t smem = batched_smem(P);
     int per_sm = 0;
-    ck_at(cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), __LINE__);
     ck_at(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, CTA_THREADS, smem), __LINE__);
     int grid = std::min(batch, num_sms() * std::max(1, per_sm));
     // device memory: descriptors, order, counter, info, per-block scratch

@@ -21,9 +21,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/schur_gb300.h"
+#include "batched.cuh"
 #include "kernels.cuh"
 #include "host.h"
 
@@ -159,8 +161,12 @@ void Solver::carve(char* base, int n) {
 // ---------------------------------------------------------------------------
 // Solver
 // ---------------------------------------------------------------------------
-static bool g_attr_done = false;
-static int g_num_sms = 0;
+// Kernel attributes are per device: they are raised once for each device,
+// under a lock, the first time a call runs with that device current.
+#define ATTR_MAX_DEVICES 64
+static std::mutex g_attr_mu;
+static bool g_attr_done[ATTR_MAX_DEVICES] = {false};
+static int g_num_sms[ATTR_MAX_DEVICES] = {0};
 
 thread_local char g_err_detail[256] = "";
 
@@ -237,12 +243,15 @@ PhaseTimer::~PhaseTimer() {
 }
 
 void init_kernel_attributes() {
-  if (g_attr_done) return;
   int dev = 0;
   ck(cudaGetDevice(&dev));
-  ck(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
-  // each kernel may take what the block limit leaves beside its static
-  // shared memory
+  if (dev < 0 || dev >= ATTR_MAX_DEVICES) throw CudaError{cudaErrorInvalidDevice};
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (g_attr_done[dev]) return;
+  ck(cudaDeviceGetAttribute(&g_num_sms[dev], cudaDevAttrMultiProcessorCount, dev));
+  // every kernel with dynamic shared memory may take what the block limit
+  // leaves beside its static shared memory; raised once and never lowered, so
+  // that no entry point changes a limit that another one relies on
   int optin = 0;
   ck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   auto allow = [&](const void* k) {
@@ -253,19 +262,30 @@ void init_kernel_attributes() {
   allow((const void*)k_chase);
   allow((const void*)k_smallqr);
   allow((const void*)k_aed_small);
+  allow((const void*)k_batched);
   ck(apply_u_set_smem(220 * 1024));
-  g_attr_done = true;
+  g_attr_done[dev] = true;
 }
 
-int num_sms() { return g_num_sms > 0 ? g_num_sms : 152; }
+int num_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= ATTR_MAX_DEVICES) {
+    cudaGetLastError();
+    return 152;
+  }
+  return g_num_sms[dev] > 0 ? g_num_sms[dev] : 152;
+}
+
+void read_opts(const schur_opts* in, schur_opts* out) {
+  schur_default_opts(out);
+  if (!in) return;
+  size_t sz = (in->struct_size <= 0) ? sizeof(schur_opts) : std::min((size_t)in->struct_size, sizeof(schur_opts));
+  memcpy(out, in, sz);
+  out->struct_size = (int)sizeof(schur_opts);
+}
 
 Solver::Solver(const schur_opts* o) {
-  schur_default_opts(&opts);
-  if (o) {
-    size_t sz = std::min((size_t)o->struct_size, sizeof(schur_opts));
-    if (sz == 0) sz = sizeof(schur_opts);
-    memcpy(&opts, o, sz);
-  }
+  read_opts(o, &opts);
   st = (cudaStream_t)opts.stream;
   timer.on = opts.timing != 0;
   if (opts.nmin <= 0) opts.nmin = 75;
@@ -848,8 +868,7 @@ extern "C" int schur_workspace_size(int n, const schur_opts* opts, size_t* bytes
   if (n < 0) return -1;
   if (!bytes) return -3;
   schur_opts o;
-  schur_default_opts(&o);
-  if (opts) memcpy(&o, opts, std::min((size_t)std::max(opts->struct_size, 0), sizeof(o)));
+  read_opts(opts, &o);
   *bytes = workspace_bytes(std::max(n, 1), o);
   return SCHUR_OK;
 }
@@ -1003,8 +1022,7 @@ extern "C" int schur_aed(int n, double* H, int ldh, double* Z, int ldz, int ktop
   if (!nd) return -9;
   try {
     schur_opts o;
-    schur_default_opts(&o);
-    if (opts) memcpy(&o, opts, std::min((size_t)std::max(opts->struct_size, 0), sizeof(o)));
+    read_opts(opts, &o);
     o.aed_window = nw;
     Solver s(&o);
     int rc = s.setup(n);

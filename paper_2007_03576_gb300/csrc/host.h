@@ -148,8 +148,11 @@ struct Solver {
 extern thread_local schur_stats g_stats;
 extern thread_local char g_err_detail[256];
 void ck_at(cudaError_t e, int line);
-void init_kernel_attributes();
-int num_sms();
+void init_kernel_attributes();   // once per device (thread-safe); throws CudaError
+int num_sms();                   // SMs of the current device
+// *out = the defaults overlaid with the first in->struct_size bytes of *in
+// (the whole struct when struct_size <= 0); in may be NULL.
+void read_opts(const schur_opts* in, schur_opts* out);
 void default_ns_nw(int m, int* ns, int* nw);
 size_t workspace_bytes(int n, const schur_opts& o);
 const char* status_string(int code);

@@ -14,9 +14,11 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/schur_gb300.h"
 #include "batched.cuh"
+#include "host.h"
 
 #define NA_NW 64                 // AED window limit of this entry point
 #define NA_NMAX 1024             // largest order accepted
@@ -35,9 +37,28 @@
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
-// Device address of g_noalloc_scratch per device (set up once per device,
-// with that device current).
+// Device address of g_noalloc_scratch per device, set up once per device
+// (with that device current) together with the kernels' shared-memory limits,
+// which are raised to their maximum there and never changed per call.
 static char* g_scratch_ptr[NA_MAX_DEVICES] = {nullptr};
+static std::mutex g_setup_mu;
+
+static int noalloc_setup(int dev) {
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (g_scratch_ptr[dev] != nullptr) return SCHUR_OK;
+  try {
+    schur::init_kernel_attributes();
+  } catch (const schur::CudaError&) {
+    return SCHUR_ERR_CUDA;
+  }
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    return SCHUR_ERR_CUDA;
+  }
+  g_scratch_ptr[dev] = (char*)p;
+  return SCHUR_OK;
+}
 
 extern "C" int schur_hessenberg_noalloc(int n, double* H, int ldh, double* Z, int ldz, double* wr, double* wi,
                                         const schur_opts* opts) {
@@ -51,18 +72,13 @@ extern "C" int schur_hessenberg_noalloc(int n, double* H, int ldh, double* Z, in
   if (!wr) return -6;
   if (!wi) return -7;
   schur_opts o;
-  schur_default_opts(&o);
-  if (opts) memcpy(&o, opts, std::min((size_t)std::max(opts->struct_size, 0), sizeof(o)));
+  schur::read_opts(opts, &o);
   cudaStream_t st = (cudaStream_t)o.stream;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return SCHUR_ERR_CUDA;
   if (g_scratch_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      return SCHUR_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = (char*)p;
+    int rc = noalloc_setup(dev);
+    if (rc != SCHUR_OK) return rc;
   }
   char* base = g_scratch_ptr[dev];
   // parameters: the built-in size table with windows capped at NA_NW
@@ -98,8 +114,7 @@ extern "C" int schur_hessenberg_noalloc(int n, double* H, int ldh, double* Z, in
   if (cudaMemcpyAsync(base + NA_OFF_COUNTER, zero2, 16, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(base + NA_OFF_ORDER, &order0, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(base + NA_OFF_DESC, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(base + NA_OFF_SCRATCH, &sc, sizeof(sc), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaMemcpyAsync(base + NA_OFF_SCRATCH, &sc, sizeof(sc), cudaMemcpyHostToDevice, st) != cudaSuccess) {
     cudaGetLastError();
     return SCHUR_ERR_CUDA;
   }

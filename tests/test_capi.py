@@ -41,6 +41,24 @@ def test_workspace_size_grows_with_n():
     assert lib.schur_workspace_size(-1, ctypes.byref(o), ctypes.byref(ctypes.c_size_t())) == -1
 
 
+def test_struct_size_zero_reads_the_whole_opts_block():
+    """struct_size <= 0 means the whole struct in every entry point: the
+    shift and window overrides of such a block change the workspace size
+    exactly as those of a block with struct_size = sizeof(schur_opts)."""
+    lib = _lib.load()
+    full = _lib.make_opts(0, n_shifts=64, aed_window=200)
+    zero = _lib.make_opts(0, n_shifts=64, aed_window=200)
+    zero.struct_size = 0
+    plain = _lib.make_opts(0)
+    got = {}
+    for name, o in (("full", full), ("zero", zero), ("plain", plain)):
+        b = ctypes.c_size_t(0)
+        assert lib.schur_workspace_size(20000, ctypes.byref(o), ctypes.byref(b)) == 0
+        got[name] = b.value
+    assert got["zero"] == got["full"]
+    assert got["zero"] != got["plain"]
+
+
 def test_argument_validation_without_gpu():
     """Invalid arguments are rejected before any device work."""
     lib = _lib.load()
