@@ -97,40 +97,70 @@ struct Mat {
 __device__ __forceinline__ double smlnum_of(int n) { return SCHUR_NU * ((double)n / SCHUR_U); }
 
 // Householder reflector (I - tau v v^T), v = (1, v1, v2) (v2 = 0 when nr == 2),
-// with (I - tau v v^T) x = beta e_1, beta = -sign(x0) ||x||.  With
-// r = 1/||x|| and d = x0 - beta: v = x / d, tau = -d / beta = sign(x0) d r,
-// so one reciprocal square root and one reciprocal suffice (fastmath.cuh);
-// operands whose squares could overflow/underflow take the hypot path.
+// with (I - tau v v^T) x = beta e_1, beta = -sign(x0) ||x||.
+//
+// This is the innermost link of every serial chain of the method (the next
+// reflector of a bulge depends on the previous one), so it is arranged for
+// the fewest dependent FP64 operations.  With r = 1/||x||:
+//   tau = (beta - x0) / beta = 1 + |x0| r,  in [1, 2];
+//   v_i = x_i / (x0 - beta) = sign(x0) x_i r / tau;
+// so one reciprocal square root (of ||x||^2) and one reciprocal of tau are
+// needed.  The FP32 seed of 1/tau is formed from the FP32 seed of r beside
+// the FP64 chain, and both are refined by one third-order Newton step
+// (fastmath.cuh): 12 dependent FP64 operations in all.  The magnitude tests
+// are integer operations, evaluated beside the chain; operands whose squares
+// could overflow or underflow take the hypot path afterwards.
 __device__ __forceinline__ void house3(int nr, double x0, double x1, double x2, double& v1, double& v2,
                                        double& tau, double& beta) {
   if (nr < 3) x2 = 0.0;
-  if (nr < 2 || (fm_abs_key(x1) | fm_abs_key(x2)) == 0) {
+  const bool trivial = nr < 2 || (fm_abs_key(x1) | fm_abs_key(x2)) == 0;
+  const bool safe = fm_safe_range3(x0, x1, x2);
+  const int h0 = __double2hiint(x0);
+  const double ax0 = fabs(x0);
+  const double a = fma(x0, x0, fma(x1, x1, x2 * x2));
+  const int ha = __double2hiint(a);
+  const int e = ((ha >> 20) & 0x7ff) - 1023;
+  const int k = e >> 1;
+  // FP32 seed of (a 2^-2k)^(-1/2), and of 1/tau from |x0| 2^-k in FP32
+  const float sf = fm_rsqrt_approx_f32(fm_mantissa_f32(ha, __double2loint(a), e & 1));
+  const double y = fm_f32_to_f64_scaled(sf, -k);
+  const int e0 = ((h0 >> 20) & 0x7ff) - 1023 - k;
+  const float x0f = (e0 < -126 || (fm_abs_key(x0) == 0))
+                        ? 0.0f
+                        : __uint_as_float(((unsigned)(e0 + 127) << 23) | (((unsigned)h0 & 0xfffffu) << 3) |
+                                          ((unsigned)__double2loint(x0) >> 29));
+  const float rtf = fm_rcp_approx_f32(fmaf(x0f, sf, 1.0f));
+  // r = a^(-1/2): one third-order step
+  const double ay = a * y;
+  const double ee = fma(-ay, y, 1.0);
+  const double ye = y * ee;
+  const double pp = fma(0.375, ee, 0.5);
+  const double r = fma(ye, pp, y);
+  tau = fma(ax0, r, 1.0);
+  const double rs = copysign(r, x0);
+  const double xr1 = x1 * rs, xr2 = x2 * rs;
+  beta = -copysign(a * r, x0);
+  // 1/tau, tau in [1, 2]: one third-order step from the FP32 seed
+  double z = fm_f32_to_f64_scaled(rtf, 0);
+  const double et = fma(-tau, z, 1.0);
+  const double pt = fma(et, et, et);
+  z = fma(z, pt, z);
+  v1 = xr1 * z;
+  v2 = xr2 * z;
+  if (trivial) {
     v1 = 0.0;
     v2 = 0.0;
     tau = 0.0;
     beta = x0;
-    return;
+  } else if (!safe) {
+    double sig = hypot(x1, x2);
+    double nrm = hypot(x0, sig);
+    beta = -copysign(nrm, x0);
+    tau = (beta - x0) / beta;
+    double den = x0 - beta;
+    v1 = x1 / den;
+    v2 = x2 / den;
   }
-  const bool neg = __double2hiint(x0) < 0;
-  if (fm_safe_range3(x0, x1, x2)) {
-    double a = fma(x0, x0, fma(x1, x1, x2 * x2));
-    double r = fast_rsqrt(a);
-    double nrm = a * r;
-    beta = neg ? nrm : -nrm;
-    double d = x0 - beta;
-    double rd = fast_rcp(d);
-    v1 = x1 * rd;
-    v2 = x2 * rd;
-    tau = neg ? -d * r : d * r;
-    return;
-  }
-  double sig = hypot(x1, x2);
-  double nrm = hypot(x0, sig);
-  beta = -copysign(nrm, x0);
-  tau = (beta - x0) / beta;
-  double den = x0 - beta;
-  v1 = x1 / den;
-  v2 = x2 / den;
 }
 
 // Eigenvalues of [[a, b], [c, d]]; for a complex pair im1 > 0.

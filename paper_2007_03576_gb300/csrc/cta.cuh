@@ -129,15 +129,27 @@ __device__ inline void cta_standardize_block(const Mat& T, int k, int ncols, con
 // One Francis double-shift sweep on [l, i] of the m x m matrix T (full Schur
 // mode within T: columns up to m-1, rows from 0), accumulated into U.
 //
-// One barrier per reflector.  The reflector of step k acts on rows k..k+2
-// (columns k..m-1) and on columns k..k+2 (rows 0..k+3 and U); the two
-// products meet only on the diagonal block (rows k..k+3, columns k..k+2).
-// Warp 0 updates that block and then builds the next step's reflector from
-// its first column (a short FP64 chain, see house3) -- the next reflector
-// needs nothing else -- while the other warps apply the current reflector to
-// the rest of rows k..k+2 and of columns k..k+2, which are disjoint.  Every
-// entry receives the same operations in the same order as with the left
-// product applied before the right one.  Reflectors alternate between two
+// The sweep is a chain: the reflector P_{k+1} is built from column k of
+// P_k T P_k, so the time of a step is the length of that chain.  On this GPU
+// a dependent FP64 operation costs ~64 cycles, and a sub-partition of the SM
+// issues one FP64 warp instruction per ~64 cycles whatever the number of
+// active lanes; so the chain runs alone on one lane of warp 0, whose
+// sub-partition does no other FP64 work, and it touches no other data than a
+// register copy of the 4 x 3 block B_k = T[k..k+3, k..k+2]:
+//   y  = column k of B_k P_k  (rows k..k+3),
+//   x  = rows k+1..k+3 of P_k y  (6 dependent operations in all),
+//   P_{k+1} = house3(x).
+// Beside it, per step (one barrier per step):
+//   - warp 1 applies P_k to the diagonal block T[k..k+3, k..k+3] (left
+//     product on rows k..k+2, then right product on columns k..k+2, so every
+//     entry receives the same operations in the same order as with the left
+//     product applied first), writes it back, and hands B_{k+1} to the chain
+//     lane through a double buffer;
+//   - the warps of the other three sub-partitions apply P_k to the rest of
+//     rows k..k+2 (columns k+4..m-1), of columns k..k+2 (rows 0..k-1) and
+//     to U.
+// These regions are disjoint; the chain lane writes the new column k
+// (beta, 0, 0) below the diagonal itself.  Reflectors alternate between two
 // slots of sh->r.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void refl3_apply(double* p, long long stride, int nr, double v1, double v2, double tau) {
@@ -148,93 +160,148 @@ __device__ __forceinline__ void refl3_apply(double* p, long long stride, int nr,
   if (nr == 3) p[2 * stride] = fma(-s, v2, a2);
 }
 
+// the warps that apply a step's reflector away from the diagonal block: all
+// but warp 0 (the chain), warp 1 (the block) and warp 4 (warp 0's
+// sub-partition)
+__device__ __forceinline__ bool francis_far_warp(int warp) { return warp >= 2 && warp != 4; }
+__device__ __forceinline__ int francis_far_rank(int warp) { return warp - 2 - (warp > 4 ? 1 : 0); }
+
 __device__ inline void cta_double_shift_sweep(const Mat& T, int m, int l, int i, double ssum, double sprod,
                                               const Mat& U, int urows, CtaShared* sh) {
-  const int tid = cta_tid(), nt = cta_nt(), lane = tid & 31;
+  __shared__ double bnext[2][16];   // B_k for the chain lane, by step parity (row r, column c at r + 4c)
+  const int tid = cta_tid(), nt = cta_nt(), lane = tid & 31, warp = tid >> 5;
+  // far warps: 2..nwarps-1 without 4 (blocks of at least 3 warps; the kernels use 8)
+  const int nwarps = nt >> 5;
+  const int nfar = nwarps - 2 - (nwarps > 4 ? 1 : 0);
+  // chain lane state: the current reflector
+  double cv1 = 0.0, cv2 = 0.0, ctau = 0.0;
   if (tid == 0) {
     const int nr = min(3, i - l + 1);
     double h00 = T(l, l), h01 = T(l, l + 1), h10 = T(l + 1, l), h11 = T(l + 1, l + 1);
     double x0 = fma(h00, h00, fma(h01, h10, fma(-ssum, h00, sprod)));
     double x1 = h10 * (h00 + h11 - ssum);
     double x2 = (nr == 3) ? h10 * T(l + 2, l + 1) : 0.0;
-    double v1, v2, tau, beta;
-    house3(nr, x0, x1, x2, v1, v2, tau, beta);
-    sh->r[0] = v1;
-    sh->r[1] = v2;
-    sh->r[2] = tau;
+    double beta;
+    house3(nr, x0, x1, x2, cv1, cv2, ctau, beta);
+    sh->r[0] = cv1;
+    sh->r[1] = cv2;
+    sh->r[2] = ctau;
+    // B_l (rows l..l+3, columns l..l+2; zero outside the block)
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 3; ++c)
+        bnext[(l & 1)][r + 4 * c] = (l + r <= i && r <= c + 1) ? T(l + r, l + c) : 0.0;
   }
   __syncthreads();
   const int nu = U.p ? urows : 0;
   for (int k = l; k < i; ++k) {
     const int nr = min(3, i - k + 1);
     const int slot = ((k - l) & 1) * 4;
-    const double v1 = sh->r[slot], v2 = sh->r[slot + 1], tau = sh->r[slot + 2];
-    if (tid < 32) {
-      if (tau != 0.0) {
-        const int cend = min(k + 2, m - 1);  // block columns k..cend (left product)
-        const int rend = min(k + 3, i);      // block rows k..rend (right product)
-        if (lane <= cend - k) refl3_apply(&T(k, k + lane), 1, nr, v1, v2, tau);
-        __syncwarp();
-        if (lane <= rend - k) refl3_apply(&T(k + lane, k), T.ld, nr, v1, v2, tau);
-        __syncwarp();
-      }
+    if (warp == 0) {
       if (lane == 0 && k + 1 < i) {
+        // here nr == 3; next reflector from column k of P_k B_k P_k
+        const double* B = bnext[k & 1];
+        const double v1 = cv1, v2 = cv2, tau = ctau;
+        const double tv1 = tau * v1, tv2 = tau * v2;
+        double y[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const double in = fma(v2, B[r + 8], fma(v1, B[r + 4], B[r]));
+          y[r] = fma(-tau, in, B[r]);
+        }
+        const double q = fma(v2, y[2], fma(v1, y[1], y[0]));
+        const double x0 = fma(-tv1, q, y[1]);
+        const double x1 = fma(-tv2, q, y[2]);
         const int k1 = k + 1, nr1 = min(3, i - k1 + 1);
-        double x0 = T(k1, k), x1 = T(k1 + 1, k), x2 = (nr1 == 3) ? T(k1 + 2, k) : 0.0;
-        double w1, w2, t1, beta;
-        house3(nr1, x0, x1, x2, w1, w2, t1, beta);
+        const double x2 = (nr1 == 3) ? y[3] : 0.0;
+        double beta;
+        house3(nr1, x0, x1, x2, cv1, cv2, ctau, beta);
         T(k1, k) = beta;
         T(k1 + 1, k) = 0.0;
         if (nr1 == 3) T(k1 + 2, k) = 0.0;
         const int s1 = 4 - slot;
-        sh->r[s1] = w1;
-        sh->r[s1 + 1] = w2;
-        sh->r[s1 + 2] = t1;
+        sh->r[s1] = cv1;
+        sh->r[s1 + 1] = cv2;
+        sh->r[s1 + 2] = ctau;
       }
-    } else if (tau != 0.0) {
-      // items: rows of U first (global memory, the longest loads), then rows
-      // 0..k-1 of T, then columns k+3..m-1 of T; each thread loads both of
-      // its items of a round before computing either
-      const int c0 = k + 3;
-      const int nB = max(0, m - c0);
-      const int total = nu + k + nB;
-      const int bt = tid - 32, bn = nt - 32;
-      for (int base = 0; base < total; base += 2 * bn) {
-        double* p[2];
-        long long sd[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int it = base + bt + h * bn;
-          if (it < nu) {
-            p[h] = &U(it, k);
-            sd[h] = U.ld;
-          } else if (it < nu + k) {
-            p[h] = &T(it - nu, k);
-            sd[h] = T.ld;
-          } else if (it < total) {
-            p[h] = &T(k, c0 + (it - nu - k));
-            sd[h] = 1;
-          } else {
-            p[h] = nullptr;
-            sd[h] = 0;
-          }
+    } else if (warp == 1) {
+      const double v1 = sh->r[slot], v2 = sh->r[slot + 1], tau = sh->r[slot + 2];
+      // lane = r + 4 c (r, c < 4): entry T(k + r, k + c) of the diagonal block
+      const int r = lane & 3, c = (lane >> 2) & 3;
+      const bool valid = lane < 16 && k + r <= i && k + c <= m - 1;
+      double a = valid ? T(k + r, k + c) : 0.0;
+      if (tau != 0.0) {
+        // left product on rows k..k+nr-1 of each column
+        const double a0 = __shfl_sync(0xffffffffu, a, 4 * c + 0);
+        const double a1 = __shfl_sync(0xffffffffu, a, 4 * c + 1);
+        const double a2 = __shfl_sync(0xffffffffu, a, 4 * c + 2);
+        const double s = tau * fma(v2, (nr == 3) ? a2 : 0.0, fma(v1, a1, a0));
+        if (r < nr) a = fma(-s, (r == 0) ? 1.0 : ((r == 1) ? v1 : v2), a);
+        // right product on columns k..k+nr-1 of each row
+        const double b0 = __shfl_sync(0xffffffffu, a, r + 0);
+        const double b1 = __shfl_sync(0xffffffffu, a, r + 4);
+        const double b2 = __shfl_sync(0xffffffffu, a, r + 8);
+        const double t = tau * fma(v2, (nr == 3) ? b2 : 0.0, fma(v1, b1, b0));
+        if (c < nr) a = fma(-t, (c == 0) ? 1.0 : ((c == 1) ? v1 : v2), a);
+      }
+      // column k below the diagonal belongs to the chain lane when a next
+      // reflector follows
+      if (valid && !(c == 0 && r >= 1 && k + 1 < i)) T(k + r, k + c) = a;
+      if (k + 1 < i) {
+        double* Bn = bnext[(k + 1) & 1];
+        if (lane < 16 && r >= 1 && c >= 1) Bn[(r - 1) + 4 * (c - 1)] = valid ? a : 0.0;
+        if (lane == 16) {
+          Bn[3] = 0.0;
+          Bn[7] = 0.0;
+          Bn[11] = (k + 4 <= i && k + 3 <= m - 1) ? T(k + 4, k + 3) : 0.0;
         }
-        double a[2][3];
+      }
+    } else if (francis_far_warp(warp)) {
+      const double v1 = sh->r[slot], v2 = sh->r[slot + 1], tau = sh->r[slot + 2];
+      if (tau != 0.0) {
+        // items: rows of U first (global memory, the longest loads), then rows
+        // 0..k-1 of T, then columns k+4..m-1 of T; each thread loads both of
+        // its items of a round before computing either
+        const int c0 = k + 4;
+        const int nB = max(0, m - c0);
+        const int total = nu + k + nB;
+        const int bt = francis_far_rank(warp) * 32 + lane, bn = nfar * 32;
+        for (int base = 0; base < total; base += 2 * bn) {
+          double* p[2];
+          long long sd[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-          if (p[h]) {
-            a[h][0] = p[h][0];
-            a[h][1] = p[h][sd[h]];
-            a[h][2] = (nr == 3) ? p[h][2 * sd[h]] : 0.0;
+          for (int h = 0; h < 2; ++h) {
+            const int it = base + bt + h * bn;
+            if (it < nu) {
+              p[h] = &U(it, k);
+              sd[h] = U.ld;
+            } else if (it < nu + k) {
+              p[h] = &T(it - nu, k);
+              sd[h] = T.ld;
+            } else if (it < total) {
+              p[h] = &T(k, c0 + (it - nu - k));
+              sd[h] = 1;
+            } else {
+              p[h] = nullptr;
+              sd[h] = 0;
+            }
           }
+          double a[2][3];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-          if (p[h]) {
-            double s = tau * fma(v2, a[h][2], fma(v1, a[h][1], a[h][0]));
-            p[h][0] = a[h][0] - s;
-            p[h][sd[h]] = fma(-s, v1, a[h][1]);
-            if (nr == 3) p[h][2 * sd[h]] = fma(-s, v2, a[h][2]);
-          }
+          for (int h = 0; h < 2; ++h)
+            if (p[h]) {
+              a[h][0] = p[h][0];
+              a[h][1] = p[h][sd[h]];
+              a[h][2] = (nr == 3) ? p[h][2 * sd[h]] : 0.0;
+            }
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            if (p[h]) {
+              double s = tau * fma(v2, a[h][2], fma(v1, a[h][1], a[h][0]));
+              p[h][0] = a[h][0] - s;
+              p[h][sd[h]] = fma(-s, v1, a[h][1]);
+              if (nr == 3) p[h][2 * sd[h]] = fma(-s, v2, a[h][2]);
+            }
+        }
       }
     }
     __syncthreads();
