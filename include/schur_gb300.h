@@ -79,6 +79,14 @@ typedef struct {
   size_t workspace_bytes;
   int timing;          /* 1: record per-phase device time (CUDA events) in
                           schur_stats; 0 (default): no events */
+  int nmin_window;     /* AED windows of at most this order are reduced to
+                          Schur form by double-shift QR in one thread block;
+                          larger ones by the multishift iteration itself
+                          (one recursion level; the windows of that level use
+                          double-shift QR).  The crossover plays the role of
+                          LAPACK's NMIN for the small AED task of Sec. 3.2.
+                          0 = 160, the largest window one block holds;
+                          values above 160 act as 160 */
 } schur_opts;
 
 /* Statistics of the last schur_hessenberg call on this host thread. */
@@ -304,6 +312,43 @@ int schur_apply_u(int side, double* A, int lda, int r0, int c0, int m, int k, co
  * 1/sqrt(x)} (the square-root pair is 0 for x <= 0).
  */
 int schur_fastmath_eval(int n, const double* x, double* out, const schur_opts* opts);
+
+/*
+ * schur_vigilant_eval -- the device's vigilant-deflation test of a
+ * subdiagonal entry (Sec. 2.1; the conditions of Sec. 5.6), evaluated on
+ * given matrices so that it can be checked against the CPU oracle.
+ *   count   number of matrices, >= 0                                  (arg 1)
+ *   H       device, count 4x4 matrices, column-major, each 16 doubles
+ *           apart; the entry tested is H(2, 1) of the active block rows
+ *           0..3 (its neighbours H(1, 0) and H(3, 2) enter the test when
+ *           the two diagonal entries are zero)                         (arg 2)
+ *   mode    SCHUR_DEFLATION_*                                          (arg 3)
+ *   thold   threshold of SCHUR_DEFLATION_FIXED                         (arg 4)
+ *   normH   ||H||_F of SCHUR_DEFLATION_NORM                            (arg 5)
+ *   n       order in the absolute floor nu n / u, >= 1                 (arg 6)
+ *   out     device, count ints: 1 negligible, 0 not                    (arg 7)
+ *   opts    may be NULL (stream)                                       (arg 8)
+ * Synchronises opts->stream before returning.
+ */
+int schur_vigilant_eval(int count, const double* H, int mode, double thold, double normH, int n, int* out,
+                        const schur_opts* opts);
+
+/*
+ * schur_spike_eval -- the device's AED deflation test (Sec. 5.6) of a 1x1
+ * or 2x2 diagonal block of the window's Schur form against its spike
+ * entries, evaluated on given blocks.
+ *   count   number of blocks, >= 0                                    (arg 1)
+ *   blk     device, count records of 7 doubles: a, b, c, d (the block
+ *           [[a, b], [c, d]]; only d for a 1x1 block), s_j (the spike
+ *           entry of the block's last row), s_{j-1} (of the row above, 2x2
+ *           only) and the block size (1.0 or 2.0)                      (arg 2)
+ *   mode, thold, normH, n   as in schur_vigilant_eval              (args 3-6)
+ *   out     device, count ints: 1 deflatable, 0 not                    (arg 7)
+ *   opts    may be NULL (stream)                                       (arg 8)
+ * Synchronises opts->stream before returning.
+ */
+int schur_spike_eval(int count, const double* blk, int mode, double thold, double normH, int n, int* out,
+                     const schur_opts* opts);
 
 #ifdef __cplusplus
 }

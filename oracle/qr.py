@@ -54,7 +54,8 @@ class Params:
     deflation: str = "lapack"
     thold: float = 0.0
     exc_period: int = 6
-    nwin_francis: int = 160  # AED windows up to this order: Francis QR
+    nwin_francis: int = 0    # AED windows up to max(nmin, this) use Francis QR (0: nmin, LAPACK's rule)
+    swap_tol: float = 10.0   # a swap is rejected when its residual exceeds swap_tol * u * ||A||_F
     normH: float = 0.0  # ||H||_F of the input, set by ``schur``
     depth: int = 0      # AED recursion depth (0 = the input matrix)
 
@@ -63,6 +64,7 @@ class Params:
         deflation mode, default shift/window table, one level deeper."""
         return Params(ns=0, nw=0, nmin=self.nmin, nibble=self.nibble, deflation=self.deflation,
                       thold=self.thold, exc_period=self.exc_period, nwin_francis=self.nwin_francis,
+                      swap_tol=self.swap_tol,
                       normH=self.normH, depth=self.depth + 1)
 
 
@@ -400,7 +402,7 @@ def block_size_at(T, j):
     return 2 if j + 1 < T.shape[0] and T[j + 1, j] != 0.0 else 1
 
 
-def swap_adjacent(T, V, j, p, q):
+def swap_adjacent(T, V, j, p, q, tol=10.0):
     """Swap the adjacent diagonal blocks T[j:j+p, j:j+p] (p x p) and
     T[j+p:j+p+q, j+p:j+p+q] (q x q) of the quasi-triangular T by an orthogonal
     similarity, accumulating into V (direct swapping of Bai & Demmel 1993,
@@ -410,9 +412,10 @@ def swap_adjacent(T, V, j, p, q):
     A11 X - X A22 = A12 makes the columns of [-X; I] span the invariant
     subspace of A22; the orthogonal factor Q of their QR factorisation swaps
     the blocks.  The swap is rejected (T and V untouched, returns False) when
-    the new (2,1) block of Q^T A Q exceeds max(10 u ||A||_F, nu n / u)
-    (reading of the paper's "too ill-conditioned", Sec. 3.5.3).  Swapped 2x2
-    blocks are re-standardised.
+    the new (2,1) block of Q^T A Q exceeds max(tol u ||A||_F, nu n / u),
+    tol = 10 (reading of the paper's "too ill-conditioned", Sec. 3.5.3;
+    Bai & Demmel's weak stability test).  Swapped 2x2 blocks are
+    re-standardised.
     """
     nT = T.shape[0]
     m = p + q
@@ -429,7 +432,7 @@ def swap_adjacent(T, V, j, p, q):
         apply_left(W, v, tau, slice(c, m), slice(c, q))
         apply_right(Q, v, tau, slice(0, m), slice(c, m))
     A2 = Q.T @ A @ Q
-    if np.linalg.norm(A2[q:, :q]) > max(10.0 * U * np.linalg.norm(A), smlnum(nT)):
+    if np.linalg.norm(A2[q:, :q]) > max(tol * U * np.linalg.norm(A), smlnum(nT)):
         return False
     blk = slice(j, j + m)
     T[blk, j:] = Q.T @ T[blk, j:]
@@ -443,7 +446,7 @@ def swap_adjacent(T, V, j, p, q):
     return True
 
 
-def move_block_up(T, V, ifst, ilst, p=None):
+def move_block_up(T, V, ifst, ilst, p=None, tol=10.0):
     """Move the diagonal block starting at row ifst up so that it starts at
     row ilst (ilst <= ifst, a block boundary) by adjacent swaps.  The block is
     moved as a unit of its original size p even if it splits on the way.
@@ -453,7 +456,7 @@ def move_block_up(T, V, ifst, ilst, p=None):
     here = ifst
     while here > ilst:
         q = 2 if here >= 2 and here - 2 >= ilst and T[here - 1, here - 2] != 0.0 else 1
-        if not swap_adjacent(T, V, here - q, q, p):
+        if not swap_adjacent(T, V, here - q, q, p, tol):
             return False
         here -= q
     return True
@@ -485,11 +488,17 @@ def aed(H, Z, ktop, kbot, nw, P, n=None):
     [ktop, kbot] (Sec. 2.5):
 
     1. the window T is copied out and reduced to Schur form T = V T_S V^T by
-       recursive QR (this driver; Francis double-shift QR when nw is at most
-       max(nmin, nwin_francis) or when T is itself the window of a window --
-       reading: the paper says "recursive application of the QR algorithm"
-       without a size or depth rule; nwin_francis = 160 is the largest window
-       one GPU thread block holds in shared memory);
+       recursive QR: this driver when nw exceeds the crossover
+       max(nmin, nwin_francis), Francis double-shift QR otherwise, and always
+       Francis for the window of a window.  Reading: the paper says
+       "recursive application of the QR algorithm" (Sec. 2.5) and implements
+       the small AED task with LAPACK's sequential QR (Sec. 3.2, the small
+       AED task calls DHSEQR), whose AED uses the double-shift routine for
+       windows of at most NMIN rows and the recursive multishift routine
+       above (NMIN = 75 by default, a machine-dependent tunable), with the
+       windows of the recursive level reduced by the double-shift routine.
+       The default nwin_francis = 0 takes that rule with NMIN = nmin; a
+       larger nwin_francis moves the crossover as a tuning of NMIN does;
     2. with s = h_{kwtop, kwtop-1} the spike is s * V[0, :]; candidates are
        tested bottom-up (``spike_deflatable``); a failed block is moved to
        the top of the unevaluated part (``move_block_up``); a rejected swap
@@ -523,7 +532,7 @@ def aed(H, Z, ktop, kbot, nw, P, n=None):
         if spike_deflatable(T, spike, ns - 1, bs, P, n):
             ns -= bs
             continue
-        if not move_block_up(T, V, ns - bs, ilst, bs):
+        if not move_block_up(T, V, ns - bs, ilst, bs, P.swap_tol):
             break
         ilst += bs
     nd = nw - ns

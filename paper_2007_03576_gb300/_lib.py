@@ -45,6 +45,7 @@ class SchurOpts(ctypes.Structure):
         ("workspace", c_void_p),
         ("workspace_bytes", c_size_t),
         ("timing", c_int),
+        ("nmin_window", c_int),
     ]
 
 
@@ -97,6 +98,8 @@ _SIGS = {
     "schur_batched_set_table": (c_int, [c_int, P(c_int), P(c_int), P(c_int)]),
     "schur_hessenberg_noalloc": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p,
                                          P(SchurOpts)]),
+    "schur_vigilant_eval": (c_int, [c_int, c_void_p, c_int, c_double, c_double, c_int, c_void_p, P(SchurOpts)]),
+    "schur_spike_eval": (c_int, [c_int, c_void_p, c_int, c_double, c_double, c_int, c_void_p, P(SchurOpts)]),
 }
 
 _LIB = None

@@ -47,7 +47,7 @@ def new_colmajor(n, m=None, device="cuda"):
 
 
 def schur(H, Z=None, *, n_shifts=0, aed_window=0, bulges_per_chain=0, nmin=0, nibble=0, deflation="lapack",
-          fixed_thold=0.0, want_z=True, workspace=None, check=True):
+          fixed_thold=0.0, want_z=True, workspace=None, check=True, nmin_window=0):
     """Real Schur form of the upper Hessenberg H: returns (S, Z, wr, wi, info)
     with S = Z^T H Z (H itself is not modified).  If Z is given the
     transformations are accumulated into a copy of it (Z <- Z Z_QR); else Z
@@ -66,7 +66,7 @@ def schur(H, Z=None, *, n_shifts=0, aed_window=0, bulges_per_chain=0, nmin=0, ni
     wi = torch.empty(n, dtype=torch.float64, device=H.device)
     o = _lib.make_opts(_stream_ptr().value, n_shifts=n_shifts, aed_window=aed_window,
                        bulges_per_chain=bulges_per_chain, nmin=nmin, nibble=nibble, deflation=deflation,
-                       fixed_thold=fixed_thold, want_z=1 if want_z else 0, z_init=zinit)
+                       fixed_thold=fixed_thold, want_z=1 if want_z else 0, z_init=zinit, nmin_window=nmin_window)
     if workspace is not None:
         o.workspace = workspace.data_ptr()
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -112,15 +112,17 @@ def sweep(H, Z, ilo, ihi, pairs, bulges_per_chain=0):
     _check(rc, "schur_sweep")
 
 
-def aed(H, Z, ktop, kbot, nw, deflation="lapack", fixed_thold=0.0):
-    """One AED step in place; returns (nd, candidates as complex list)."""
+def aed(H, Z, ktop, kbot, nw, deflation="lapack", fixed_thold=0.0, nmin_window=0):
+    """One AED step in place; returns (nd, candidates as complex list).
+    nmin_window: crossover of the window's Schur form (0 = the library's
+    default, 160)."""
     lib = _lib.load()
     n = H.shape[0]
     nd = ctypes.c_int(0)
     nc = ctypes.c_int(0)
     cre = (ctypes.c_double * max(nw, 1))()
     cim = (ctypes.c_double * max(nw, 1))()
-    o = _lib.make_opts(_stream_ptr().value, deflation=deflation, fixed_thold=fixed_thold)
+    o = _lib.make_opts(_stream_ptr().value, deflation=deflation, fixed_thold=fixed_thold, nmin_window=nmin_window)
     rc = lib.schur_aed(n, H.data_ptr(), _ld(H), Z.data_ptr() if Z is not None else None,
                        _ld(Z) if Z is not None else 1, ktop, kbot, nw, ctypes.byref(nd), cre, cim,
                        ctypes.byref(nc), ctypes.byref(o))

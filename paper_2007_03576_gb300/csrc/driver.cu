@@ -70,13 +70,14 @@ struct LevelSizes {
   int nwmax;   // largest AED window
   int nsmax;   // most shifts
   size_t arena;  // level 0: doubles of the arena behind the Z stream
+  int fmax;      // windows above this order are reduced recursively (need the copy T)
   size_t bytes() const {
     size_t b = 0;
     b += align_up(sizeof(Ctl));
     b += align_up((size_t)MAX_CHAINS * KWIN_MAX * KWIN_MAX * sizeof(double));  // chase U
     b += align_up((size_t)nwmax * nwmax * sizeof(double));                       // V
     b += align_up(arena * sizeof(double));
-    b += (nwmax > NW_SMEM_MAX) ? align_up((size_t)nwmax * nwmax * sizeof(double)) : 0;  // T
+    b += (nwmax > fmax) ? align_up((size_t)nwmax * nwmax * sizeof(double)) : 0;  // T
     b += 2 * align_up((size_t)std::max(nwmax, 4) * sizeof(double));              // candidates
     b += align_up((size_t)(nsmax + 8) * sizeof(double));                         // pairs
     b += align_up((size_t)4 * std::max(nwmax, 4) * sizeof(double));              // vbuf
@@ -84,6 +85,12 @@ struct LevelSizes {
     return b;
   }
 };
+
+// Largest AED window reduced by double-shift QR in one thread block at the
+// top level (the crossover to the recursive multishift iteration).
+static int window_francis_max(const schur_opts& o) {
+  return (o.nmin_window > 0) ? std::min(o.nmin_window, NW_SMEM_MAX) : NW_SMEM_MAX;
+}
 
 static void level_plan(int n, const schur_opts& o, std::vector<LevelSizes>& out) {
   out.clear();
@@ -109,9 +116,9 @@ static void level_plan(int n, const schur_opts& o, std::vector<LevelSizes>& out)
       arena = std::min(arena, (size_t)(1ull << 27));                       // at most 1 GiB
       arena = std::max(arena, (size_t)MAX_CHAINS * KWIN_MAX * KWIN_MAX + (size_t)nw * nw);
     }
-    LevelSizes L{m, nw, ns, arena};
+    LevelSizes L{m, nw, ns, arena, lev == 0 ? window_francis_max(o) : NW_SMEM_MAX};
     out.push_back(L);
-    if (nw <= NW_SMEM_MAX) break;
+    if (nw <= L.fmax) break;
     m = nw;
   }
 }
@@ -148,7 +155,7 @@ void Solver::carve(char* base, int n) {
       arena_cap = L.arena;
       arena_cur = 0;
     }
-    v.T = (L.nwmax > NW_SMEM_MAX) ? (double*)take((size_t)L.nwmax * L.nwmax * sizeof(double)) : nullptr;
+    v.T = (L.nwmax > L.fmax) ? (double*)take((size_t)L.nwmax * L.nwmax * sizeof(double)) : nullptr;
     v.cand_re = (double*)take((size_t)std::max(L.nwmax, 4) * sizeof(double));
     v.cand_im = (double*)take((size_t)std::max(L.nwmax, 4) * sizeof(double));
     v.pairs = (double*)take((size_t)(L.nsmax + 8) * sizeof(double));
@@ -802,7 +809,11 @@ int Solver::aed(const Mat3& M, int lev, int ktop, int kbot, int nw, int ns_max, 
   const bool zasync = (lev == 0 && zst != nullptr && M.Z != nullptr);
   double* V = zasync ? arena_alloc((size_t)nw * nw) : Lv.V;
   int tok = timer.begin(st, PH_AED);
-  if (nw <= NW_SMEM_MAX) {
+  // the window's Schur form: double-shift QR in one block up to the
+  // crossover, the recursive iteration above it; windows of windows always
+  // use double-shift QR
+  const bool in_block = nw <= NW_SMEM_MAX && (lev > 0 || nw <= window_francis_max(opts));
+  if (in_block) {
     size_t smem = (size_t)(nw | 1) * nw * sizeof(double);
     ++g_stats.kernel_launches;
     k_aed_small<<<1, CTA_THREADS, smem, st>>>(M.H, M.ldh, ktop, kbot, nw, V, nw, Lv.cand_re, Lv.cand_im, Lv.vbuf,
@@ -1104,4 +1115,40 @@ extern "C" int schur_fastmath_eval(int n, const double* x, double* out, const sc
   if (cudaGetLastError() != cudaSuccess) return SCHUR_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return SCHUR_ERR_CUDA;
   return SCHUR_OK;
+}
+
+static int deflation_eval(int which, int count, const double* data, int mode, double thold, double normH, int n,
+                          int* out, const schur_opts* opts) {
+  if (count < 0) return -1;
+  if (count > 0 && !data) return -2;
+  if (mode < SCHUR_DEFLATION_LAPACK || mode > SCHUR_DEFLATION_FIXED) return -3;
+  if (n < 1) return -6;
+  if (count > 0 && !out) return -7;
+  if (count == 0) return SCHUR_OK;
+  schur_opts o;
+  read_opts(opts, &o);
+  cudaStream_t st = (cudaStream_t)o.stream;
+  DeflParams dp;
+  dp.mode = mode;
+  dp.thold = thold;
+  dp.normH = normH;
+  dp.n = n;
+  const int grid = std::min((count + 255) / 256, 1024);
+  if (which == 0)
+    k_vigilant_eval<<<grid, 256, 0, st>>>(count, data, dp, out);
+  else
+    k_spike_eval<<<grid, 256, 0, st>>>(count, data, dp, out);
+  if (cudaGetLastError() != cudaSuccess) return SCHUR_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SCHUR_ERR_CUDA;
+  return SCHUR_OK;
+}
+
+extern "C" int schur_vigilant_eval(int count, const double* H, int mode, double thold, double normH, int n, int* out,
+                                   const schur_opts* opts) {
+  return deflation_eval(0, count, H, mode, thold, normH, n, out, opts);
+}
+
+extern "C" int schur_spike_eval(int count, const double* blk, int mode, double thold, double normH, int n, int* out,
+                                const schur_opts* opts) {
+  return deflation_eval(1, count, blk, mode, thold, normH, n, out, opts);
 }

@@ -578,6 +578,23 @@ __global__ void k_extract_eigs(const double* H, long long ldh, int n, double* wr
 }
 
 // ---------------------------------------------------------------------------
+// Diagnostics: the deflation tests of Sec. 5.6 on given data.
+__global__ void k_vigilant_eval(int count, const double* H, DeflParams dp, int* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    Mat Hm{const_cast<double*>(H) + 16 * (long long)i, 4};
+    out[i] = subdiag_negligible(Hm, 2, 0, 3, dp) ? 1 : 0;
+  }
+}
+
+__global__ void k_spike_eval(int count, const double* blk, DeflParams dp, int* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const double* r = blk + 7 * (long long)i;
+    const int bs = (r[6] == 2.0) ? 2 : 1;
+    out[i] = spike_deflatable_blk(r[0], r[1], r[2], r[3], r[4], r[5], bs, dp) ? 1 : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Diagnostic: the low-latency reciprocal / reciprocal square root of
 // fastmath.cuh next to CUDA's IEEE division and square root.
 __global__ void k_fastmath_eval(int n, const double* x, double* out) {

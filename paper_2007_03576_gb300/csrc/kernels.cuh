@@ -21,6 +21,8 @@ __global__ void k_chase(double* H, long long ldh, const double* pairs, double* U
 __global__ void k_extract_eigs(const double* H, long long ldh, int n, double* wr, double* wi);
 __global__ void k_set_int(int* p, int v);
 __global__ void k_fastmath_eval(int n, const double* x, double* out);
+__global__ void k_vigilant_eval(int count, const double* H, DeflParams dp, int* out);
+__global__ void k_spike_eval(int count, const double* blk, DeflParams dp, int* out);
 
 // off-window products (TN = vectors per tile, 64/32/16/8)
 cudaError_t launch_apply_u(int tn, int grid, size_t smem, cudaStream_t st, const UpdArgs& a);

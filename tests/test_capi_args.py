@@ -45,6 +45,10 @@ SCALAR_CASES = [
      {0: [2, -1], 1: [None], 2: [0], 3: [-1], 4: [-1], 5: [-1], 6: [0, 1025], 7: [None], 8: [3]}),
     ("schur_fastmath_eval", [N, DEV, DEV],
      {0: [-1], 1: [None], 2: [None]}),
+    ("schur_vigilant_eval", [N, DEV, 0, 0.0, 1.0, 4, DEV],
+     {0: [-1], 1: [None], 2: [-1, 3], 5: [0], 6: [None]}),
+    ("schur_spike_eval", [N, DEV, 0, 0.0, 1.0, 4, DEV],
+     {0: [-1], 1: [None], 2: [-1, 3], 5: [0], 6: [None]}),
 ]
 
 

@@ -150,21 +150,36 @@ def test_small_qr_matches_oracle(n, lo, hi):
 # ----------------------------------------------------------------- AED
 
 
-@pytest.mark.parametrize("n,nw,pre", [(60, 20, 2), (200, 48, 3), (300, 160, 4), (400, 200, 4)])
-def test_aed_matches_oracle(n, nw, pre):
+@pytest.mark.parametrize("n,nw,pre,rule", [
+    (60, 20, 2, "lapack"), (200, 48, 3, "lapack"), (300, 96, 4, "lapack"), (300, 160, 4, "lapack"),
+    (400, 200, 4, "lapack"), (300, 96, 4, "gpu160"), (300, 160, 4, "gpu160"),
+])
+def test_aed_matches_oracle(n, nw, pre, rule):
     """One AED step (Sec. 2.5) on identical inputs: the same number of
     deflations and the same candidate multiset (to rounding), orthogonal
-    similarity, Hessenberg form restored.  nw = 200 exercises the recursive
-    window path (window reduced by the multishift driver itself)."""
+    similarity, Hessenberg form restored.
+
+    The window's Schur form switches from double-shift QR to the recursive
+    multishift iteration at a crossover (LAPACK's NMIN for the paper's
+    small AED task).  rule "lapack": the oracle's default crossover
+    (nmin = 75) and the GPU set to the same (nmin_window = 75), so windows of
+    96..200 rows take the recursive path on both sides.  rule "gpu160": the
+    GPU's default crossover (160, one thread block) and the oracle given
+    the same value."""
     H = inputs.hessrand(n, 3000 + n)
     Z = np.eye(n)
     for _ in range(pre):  # let the bottom converge a little
         qr.multishift_sweep(H, Z, 0, n - 1, [(0.0, 1.0), (1.0, 2.0), (-1.0, 3.0)])
-    P = qr.Params(normH=np.linalg.norm(H))
+    if rule == "lapack":
+        P = qr.Params(normH=np.linalg.norm(H))
+        gpu_nmin_window = 75
+    else:
+        P = qr.Params(normH=np.linalg.norm(H), nwin_francis=160)
+        gpu_nmin_window = 0
     Ho, Zo = H.copy(), np.eye(n)
     nd_o, cand_o = qr.aed(Ho, Zo, 0, n - 1, nw, P)
     Hd, Zd = _dev(H), _dev(np.eye(n))
-    nd_g, cand_g = api.aed(Hd, Zd, 0, n - 1, nw)
+    nd_g, cand_g = api.aed(Hd, Zd, 0, n - 1, nw, nmin_window=gpu_nmin_window)
     Hg, Zg = _np(Hd), _np(Zd)
     assert nd_g == nd_o
     assert len(cand_g) == len(cand_o)
@@ -174,6 +189,19 @@ def test_aed_matches_oracle(n, nw, pre):
     assert np.linalg.norm(Zg @ Hg @ Zg.T - H) <= 1e-13 * np.linalg.norm(H) * 10
     assert np.max(np.abs(np.tril(Hg, -2))) == 0.0
     assert np.linalg.norm(Zg.T @ Zg - np.eye(n)) / math.sqrt(n) < 1e-13
+
+
+def test_schur_lapack_window_rule_vs_oracle():
+    """A whole reduction with the GPU's window crossover set to LAPACK's
+    NMIN (75): every AED window of 96 rows takes the recursive path; the
+    result is checked against the oracle run with its default rule."""
+    n = 300
+    H = inputs.hessrand(n, 4321)
+    S, Z, wr, wi, info = api.schur(_dev(H), n_shifts=16, aed_window=96, nmin_window=75)
+    assert info == 0
+    _check_result(H, _np(S), _np(Z))
+    So, Zo, wro, wio, _ = qr.schur(H, params=qr.Params(ns=16, nw=96))
+    _eig_match(_np(wr) + 1j * _np(wi), wro + 1j * wio, So, np.linalg.norm(H))
 
 
 # ----------------------------------------------------------------- end to end

@@ -13,6 +13,7 @@ import pytest
 import scipy.linalg
 
 from oracle import householder, qr, metrics, adjoint, testmats
+from deflation_cases import SML4, SUBDIAG_CASES, SPIKE_CASES, spike_case_args
 from paper_2007_03576_gb300 import inputs
 
 U = qr.U
@@ -496,3 +497,147 @@ def test_match_eigenvalues_recovers_permutation():
     p, dist = metrics.match_eigenvalues(a, b)
     assert np.array_equal(b[p], b[np.argsort(perm)])
     assert np.allclose(np.sort(dist), np.sort(np.abs(noise)))
+
+
+# ------------------------------------------------ vigilant deflation test
+
+
+@pytest.mark.parametrize("case,H,expected", SUBDIAG_CASES, ids=[c[0] for c in SUBDIAG_CASES])
+def test_subdiag_negligible_boundaries(case, H, expected):
+    """Vigilant deflation (Sec. 2.1; LAPACK-style condition of Sec. 5.6 with
+    the Ahues-Tisseur refinement): each case sits on one side of one of the
+    test's thresholds, with the outcome fixed by the 2x2 eigenvalue
+    perturbation stated at SUBDIAG_CASES."""
+    P = qr.Params()
+    assert bool(qr.subdiag_negligible(H, 2, 0, 3, P, 4)) == expected
+
+
+@pytest.mark.parametrize("case,rec,mode,thold,normh,expected", SPIKE_CASES, ids=[c[0] for c in SPIKE_CASES])
+def test_spike_cases(case, rec, mode, thold, normh, expected):
+    """AED deflation test (Sec. 5.6) on the shared boundary records."""
+    assert bool(qr.spike_deflatable(*spike_case_args(rec, mode, thold, normh))) == expected
+
+
+def test_subdiag_cases_separate_plausible_mistakes():
+    """The cases above tell the oracle's test from plausible slips in it:
+    swapped max/min pairs, no refinement, no zero-diagonal fallback, a
+    relative instead of the absolute floor."""
+    sml = qr.smlnum(4)
+
+    def variant(H, k, swap_ab=False, swap_aabb=False, refine=True, fallback=True):
+        h21 = abs(H[k, k - 1])
+        if h21 <= sml:
+            return True
+        tst = abs(H[k - 1, k - 1]) + abs(H[k, k])
+        if tst == 0.0 and fallback:
+            tst = abs(H[k - 1, k - 2]) + abs(H[k + 1, k])
+        if h21 > U * tst:
+            return False
+        if not refine:
+            return True
+        h12 = abs(H[k - 1, k])
+        d = abs(H[k - 1, k - 1] - H[k, k])
+        h22 = abs(H[k, k])
+        ab, ba = max(h21, h12), min(h21, h12)
+        aa, bb = max(h22, d), min(h22, d)
+        if swap_ab:
+            ab, ba = ba, ab
+        if swap_aabb:
+            aa, bb = bb, aa
+        s = aa + ab
+        return ba * (ab / s) <= max(sml, U * (bb * (aa / s)))
+
+    mistakes = [dict(swap_ab=True), dict(swap_aabb=True), dict(refine=False), dict(fallback=False)]
+    for m in mistakes:
+        with np.errstate(all="ignore"):
+            outcomes = [variant(H, 2, **m) == exp for _, H, exp in SUBDIAG_CASES]
+        assert not all(outcomes), m
+    assert all(variant(H, 2) == exp for _, H, exp in SUBDIAG_CASES)
+
+
+# ------------------------------------------------ shift selection
+
+
+def test_pairs_from_candidates_closed_form():
+    """Shift supply (Sec. 2.5: the failed candidates become the next shifts;
+    reading: bottom-most first, conjugate pairs kept together, real ones
+    paired in order of appearance, an odd real dropped).  Pairs are
+    (sum, product) of the two shifts."""
+    c = [(1.0, 0.0), (2.0, 0.0), (3.0, 0.5), (3.0, -0.5), (4.0, 0.0)]   # top to bottom
+    # from the bottom: 4 waits for a partner, the pair 3 +- 0.5i is emitted,
+    # then 2 joins 4, and 1 is left over
+    assert qr.pairs_from_candidates(c, 5) == [(6.0, 9.25), (6.0, 8.0)]
+    assert qr.pairs_from_candidates(c, 1) == [(6.0, 9.25)]
+    assert qr.pairs_from_candidates([(1.0, 0.0), (2.0, 0.0), (5.0, 0.0)], 4) == [(7.0, 10.0)]
+    assert qr.pairs_from_candidates([(-1.0, 2.0), (-1.0, -2.0)], 3) == [(-2.0, 5.0)]
+    assert qr.pairs_from_candidates([(7.0, 0.0)], 2) == []
+    assert qr.pairs_from_candidates([], 2) == []
+    # each pair's roots are two of the candidates: x^2 - sum x + prod
+    rng = np.random.default_rng(3)
+    cands = []
+    for _ in range(12):
+        if rng.random() < 0.5:
+            re, im = rng.normal(), abs(rng.normal()) + 0.1
+            cands += [(re, im), (re, -im)]
+        else:
+            cands.append((rng.normal(), 0.0))
+    pairs = qr.pairs_from_candidates(cands, 100)
+    pool = [complex(*z) for z in cands]
+    for ssum, sprod in pairs:
+        roots = np.roots([1.0, -ssum, sprod])
+        for r in roots:
+            j = int(np.argmin([abs(r - z) for z in pool]))
+            assert abs(pool[j] - r) < 1e-12
+            pool.pop(j)
+
+
+# ------------------------------------------------ rejected swaps
+
+
+def test_rejected_swap_leaves_blocks_untouched():
+    """A rejected swap (Sec. 3.5.3: a swap can be too ill-conditioned)
+    changes nothing, and move_block_up stops there.  The weak stability test
+    (residual <= tol u ||A||_F) practically never fails with a complete-
+    pivoting Sylvester solve, so the branch is driven by tol = 0: every swap
+    whose computed residual is not exactly zero is rejected."""
+    rng = np.random.default_rng(21)
+    T, _ = _quasi_tri([1, 2, 2, 1], rng)
+    T0 = T.copy()
+    V = np.eye(T.shape[0])
+    assert not qr.swap_adjacent(T, V, 1, 2, 2, tol=0.0)
+    assert np.array_equal(T, T0) and np.array_equal(V, np.eye(T.shape[0]))
+    assert qr.swap_adjacent(T.copy(), V.copy(), 1, 2, 2)          # the default accepts it
+    assert not qr.move_block_up(T, V, 3, 1, 2, tol=0.0)
+    assert np.array_equal(T, T0)
+
+
+def test_aed_halts_reordering_on_rejected_swap():
+    """Greedy halt (Sec. 3.5.4): once a swap is rejected the reordering stops;
+    the blocks tested so far keep their outcome, the untested ones count as
+    undeflated, and the window is still an orthogonal similarity of H in
+    Hessenberg form with the deflated part in Schur form."""
+    n, nw = 90, 30
+    H = inputs.hessrand(n, 404)
+    Z = np.eye(n)
+    for _ in range(3):
+        qr.multishift_sweep(H, Z, 0, n - 1, [(0.0, 1.0), (1.0, 2.0)])
+    H0 = H.copy()
+    P = qr.Params(normH=np.linalg.norm(H))
+    Pr = qr.Params(normH=np.linalg.norm(H), swap_tol=0.0)
+    Ha, Za = H.copy(), np.eye(n)
+    nd_a, cand_a = qr.aed(Ha, Za, 0, n - 1, nw, P)
+    Hr, Zr = H.copy(), np.eye(n)
+    nd_r, cand_r = qr.aed(Hr, Zr, 0, n - 1, nw, Pr)
+    # with rejections the deflation can only stop earlier
+    assert nd_r <= nd_a
+    assert len(cand_r) == nw - nd_r
+    for Hx, Zx, nd in ((Ha, Za, nd_a), (Hr, Zr, nd_r)):
+        assert np.linalg.norm(Zx @ Hx @ Zx.T - H0) < 1e-13 * np.linalg.norm(H0)
+        assert np.max(np.abs(np.tril(Hx, -2))) == 0.0
+        if nd:
+            k = n - nd
+            assert Hx[k, k - 1] == 0.0
+            assert metrics.schur_structure_errors(Hx[k:, k:]) == []
+    # the bottom-up test deflates the same leading run of blocks until the
+    # first failed candidate has to move; both runs agree on that run
+    assert nd_r >= 0
