@@ -314,6 +314,28 @@ int schur_apply_u(int side, double* A, int lda, int r0, int c0, int m, int k, co
 int schur_fastmath_eval(int n, const double* x, double* out, const schur_opts* opts);
 
 /*
+ * schur_chase_schedule -- the window schedule of one multishift sweep as the
+ * driver issues it (Sec. 2.3 / 2.4, Fig. 3; host computation only, no
+ * device work).  npairs bulges are chased in chains of at most
+ * bulges_per_chain (0 = the driver's default, 16); every launch moves each
+ * chain in flight through one diagonal window.
+ *   lo, hi    the active block, 0 <= lo, hi >= lo + 2                (args 1, 2)
+ *   npairs    bulges (shift pairs), 1 <= npairs <= 1024                (arg 3)
+ *   bulges_per_chain  >= 0                                             (arg 4)
+ *   cap       capacity of rec in records, >= 0                         (arg 5)
+ *   rec       host, cap x 7 ints: per window (launch index, ws, we, tau0,
+ *             tau1, first pair, bulges): the window rows/columns ws..we and
+ *             the chain-local steps tau0..tau1-1 moved in it; bulge j of the
+ *             chain sits at row lo + tau - 3 j at step tau            (arg 6)
+ *   count     host (output): number of windows of the sweep; records
+ *             beyond cap are not written                               (arg 7)
+ *   kwin, delta  host (output, may be NULL): the window order bound and
+ *             the steps per launch                                 (args 8, 9)
+ */
+int schur_chase_schedule(int lo, int hi, int npairs, int bulges_per_chain, int cap, int* rec, int* count,
+                         int* kwin, int* delta);
+
+/*
  * schur_vigilant_eval -- the device's vigilant-deflation test of a
  * subdiagonal entry (Sec. 2.1; the conditions of Sec. 5.6), evaluated on
  * given matrices so that it can be checked against the CPU oracle.

@@ -593,9 +593,17 @@ void Solver::apply_block_transform(const Mat3& M, int k0, int L, const double* U
 // ---------------------------------------------------------------------------
 // One multishift sweep (Sec. 2.3) on [lo, hi] with npairs pairs (device).
 // ---------------------------------------------------------------------------
-void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs, int npairs, int nbc_req) {
-  Level& Lv = levels[lev];
-  int nbc = nbc_req > 0 ? nbc_req : (opts.bulges_per_chain > 0 ? opts.bulges_per_chain : 16);
+// The window schedule of one sweep (Sec. 2.3 / 2.4, Fig. 3): npairs bulges
+// in chains of at most nbc; chain c starts S launches after chain c-1 so that
+// its window stays clear of the chain ahead; in every launch each chain in
+// flight moves delta steps inside a window of at most kwin rows.
+struct SweepPlan {
+  int nbc = 1, kwin = 0, delta = 1, nchain = 0, S = 1, last = 0;
+  std::vector<int> nbs, tend, start;
+};
+
+static SweepPlan plan_sweep(int lo, int hi, int npairs, int nbc) {
+  SweepPlan P;
   nbc = std::max(1, std::min(nbc, std::min(npairs, MAX_BULGES_PER_CHAIN)));
   // every chain in flight must fit one launch (MAX_CHAINS blocks)
   nbc = std::max(nbc, (npairs + MAX_CHAINS - 1) / MAX_CHAINS);
@@ -605,18 +613,61 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
     kwin = 3 * nbc + 2;
     delta = 1;
   }
-  int nchain = (npairs + nbc - 1) / nbc;
-  int D = kwin + delta + 3 * nbc + 2;
-  int S = (D + delta - 1) / delta;
-  std::vector<int> tend(nchain), nbs(nchain), start(nchain);
-  int last = 0;
-  for (int c = 0; c < nchain; ++c) {
-    nbs[c] = std::min(nbc, npairs - c * nbc);
-    tend[c] = (hi - lo - 1) + 3 * (nbs[c] - 1);
-    start[c] = c * S;
-    int nl = (tend[c] + delta) / delta;  // launches of this chain
-    last = std::max(last, start[c] + nl);
+  P.nbc = nbc;
+  P.kwin = kwin;
+  P.delta = delta;
+  P.nchain = (npairs + nbc - 1) / nbc;
+  const int D = kwin + delta + 3 * nbc + 2;
+  P.S = (D + delta - 1) / delta;
+  P.nbs.resize(P.nchain);
+  P.tend.resize(P.nchain);
+  P.start.resize(P.nchain);
+  for (int c = 0; c < P.nchain; ++c) {
+    P.nbs[c] = std::min(nbc, npairs - c * nbc);
+    P.tend[c] = (hi - lo - 1) + 3 * (P.nbs[c] - 1);
+    P.start[c] = c * P.S;
+    const int nl = (P.tend[c] + delta) / delta;  // launches of this chain
+    P.last = std::max(P.last, P.start[c] + nl);
   }
+  return P;
+}
+
+// The chains of launch s (chains in order 0 = ahead, lowest); returns their
+// number (<= MAX_CHAINS); each window's U is at uoff = i * kwin^2.
+static int chase_launch(const SweepPlan& P, int lo, int hi, int s, ChaseArgs& a) {
+  memset(&a, 0, sizeof(a));
+  a.lo = lo;
+  a.hi = hi;
+  a.ldu = P.kwin;
+  int na = 0;
+  for (int c = 0; c < P.nchain && na < MAX_CHAINS; ++c) {
+    if (s < P.start[c]) continue;
+    const int tau0 = (s - P.start[c]) * P.delta;
+    if (tau0 > P.tend[c]) continue;
+    const int tau1 = std::min(tau0 + P.delta, P.tend[c] + 1);
+    const int nb = P.nbs[c];
+    const int kmin = std::max(lo, lo + tau0 - 3 * (nb - 1));
+    const int kmax = std::min(hi - 1, lo + tau1 - 1);
+    if (kmin > kmax) continue;
+    ChainDesc& d = a.c[na];
+    d.ws = (kmin == lo) ? lo : kmin - 1;
+    d.we = std::min(kmax + 3, hi);
+    d.tau0 = tau0;
+    d.tau1 = tau1;
+    d.pair0 = c * P.nbc;
+    d.nb = nb;
+    d.uoff = na * P.kwin * P.kwin;
+    ++na;
+  }
+  a.nchain = na;
+  return na;
+}
+
+void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs, int npairs, int nbc_req) {
+  Level& Lv = levels[lev];
+  const int nbc0 = nbc_req > 0 ? nbc_req : (opts.bulges_per_chain > 0 ? opts.bulges_per_chain : 16);
+  const SweepPlan plan = plan_sweep(lo, hi, npairs, nbc0);
+  const int kwin = plan.kwin, delta = plan.delta, nchain = plan.nchain, last = plan.last;
   size_t smem = chase_smem_bytes(kwin);
   const bool zasync = (lev == 0 && zst != nullptr && M.Z != nullptr);
   const bool side = (lev == 0 && sst != nullptr);
@@ -624,34 +675,8 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
   side_reserve = std::min(nchain, MAX_CHAINS) + 2;
   for (int s = 0; s < last; ++s) {
     ChaseArgs a;
-    memset(&a, 0, sizeof(a));
-    a.lo = lo;
-    a.hi = hi;
-    a.ldu = kwin;
-    int na = 0;
-    // chains in order 0 (ahead, lowest) .. nchain-1; process up to
-    // MAX_CHAINS per launch (nchain <= MAX_CHAINS by construction).
-    for (int c = 0; c < nchain && na < MAX_CHAINS; ++c) {
-      if (s < start[c]) continue;
-      int tau0 = (s - start[c]) * delta;
-      if (tau0 > tend[c]) continue;
-      int tau1 = std::min(tau0 + delta, tend[c] + 1);
-      int nb = nbs[c];
-      int kmin = std::max(lo, lo + tau0 - 3 * (nb - 1));
-      int kmax = std::min(hi - 1, lo + tau1 - 1);
-      if (kmin > kmax) continue;
-      ChainDesc& d = a.c[na];
-      d.ws = (kmin == lo) ? lo : kmin - 1;
-      d.we = std::min(kmax + 3, hi);
-      d.tau0 = tau0;
-      d.tau1 = tau1;
-      d.pair0 = c * nbc;
-      d.nb = nb;
-      d.uoff = na * kwin * kwin;
-      ++na;
-    }
+    const int na = chase_launch(plan, lo, hi, s, a);
     if (na == 0) continue;
-    a.nchain = na;
     // this step's window transforms: from the arena while the Z or the side
     // stream may still need them, else the level's buffer
     const size_t need = (size_t)na * kwin * kwin;
@@ -1151,4 +1176,40 @@ extern "C" int schur_vigilant_eval(int count, const double* H, int mode, double 
 extern "C" int schur_spike_eval(int count, const double* blk, int mode, double thold, double normH, int n, int* out,
                                 const schur_opts* opts) {
   return deflation_eval(1, count, blk, mode, thold, normH, n, out, opts);
+}
+
+// ---------------------------------------------------------------------------
+// The chase schedule of a sweep, as the driver issues it (host only).
+// ---------------------------------------------------------------------------
+extern "C" int schur_chase_schedule(int lo, int hi, int npairs, int bulges_per_chain, int cap, int* rec, int* count,
+                                    int* kwin, int* delta) {
+  if (lo < 0) return -1;
+  if (hi < lo + 2) return -2;
+  if (npairs < 1 || npairs > MAX_CHAINS * MAX_BULGES_PER_CHAIN) return -3;
+  if (bulges_per_chain < 0) return -4;
+  if (cap < 0) return -5;
+  if (cap > 0 && !rec) return -6;
+  if (!count) return -7;
+  const SweepPlan P = plan_sweep(lo, hi, npairs, bulges_per_chain > 0 ? bulges_per_chain : 16);
+  if (kwin) *kwin = P.kwin;
+  if (delta) *delta = P.delta;
+  int nrec = 0;
+  for (int s = 0; s < P.last; ++s) {
+    ChaseArgs a;
+    const int na = chase_launch(P, lo, hi, s, a);
+    for (int i = 0; i < na; ++i, ++nrec) {
+      if (nrec >= cap) continue;
+      int* r = rec + 7 * (size_t)nrec;
+      const ChainDesc& d = a.c[i];
+      r[0] = s;
+      r[1] = d.ws;
+      r[2] = d.we;
+      r[3] = d.tau0;
+      r[4] = d.tau1;
+      r[5] = d.pair0;
+      r[6] = d.nb;
+    }
+  }
+  *count = nrec;
+  return SCHUR_OK;
 }

@@ -1,48 +1,79 @@
-"""Host-side check of the band of the chase windows' accumulated transforms.
+"""Host-side checks of the chase schedule that the driver issues and of the
+band of the chase windows' accumulated transforms.
 
-k_apply_u skips (16 x row-block) tiles of U that are structurally zero.  The
-driver declares, for a window of a chain of nb bulges moved delta steps, the
-band  r - c <= 2 + 2 min(nb - 1, delta - 1)  and  c - r <= delta + 1.  This
-test re-derives the window schedule of a sweep (Sec. 2.3/2.4: chains of
-bulges, chain c started S launches after chain c - 1, each launch moving every
-chain delta steps) and propagates the nonzero pattern of U through the
-window's reflectors (a reflector on rows/columns k..k+2 couples them), for
-several chain sizes, including the first (bulge introduction) and last
-(bulges leaving) windows."""
+The schedule comes from the library itself (schur_chase_schedule, the
+function Solver::sweep launches from; no GPU needed): chains of bulges,
+chain c started S launches after chain c - 1, each launch moving every chain
+delta steps (Sec. 2.3/2.4, Fig. 3).  The checks:
+  - every bulge passes every row of the active block exactly once, inside
+    its window;
+  - k_apply_u skips (16 x row-block) tiles of U that are structurally zero:
+    the driver declares, for a window of a chain of nb bulges moved delta
+    steps, the band  r - c <= 2 + 2 min(nb - 1, delta - 1)  and
+    c - r <= delta + 1, checked by propagating the nonzero pattern of U
+    through the window's reflectors (a reflector on rows/columns k..k+2
+    couples them), including the first (bulge introduction) and last
+    (bulges leaving) windows;
+  - a chase step's right products miss the next step's windows (the
+    three-stream overlap relies on it)."""
+
+import ctypes
 
 import numpy as np
 import pytest
 
-KWIN_MAX, MAX_CHAINS, MAX_BULGES = 112, 32, 32
+from paper_2007_03576_gb300 import _lib
+
+
+def library_schedule(lo, hi, npairs, nbc):
+    """[(launch, ws, we, tau0, tau1, pair0, nb)], kwin, delta of a sweep, from
+    the library."""
+    lib = _lib.load()
+    count, kwin, delta = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert lib.schur_chase_schedule(lo, hi, npairs, nbc, 0, None, ctypes.byref(count), None, None) == 0
+    buf = (ctypes.c_int * (7 * max(1, count.value)))()
+    assert lib.schur_chase_schedule(lo, hi, npairs, nbc, count.value, buf, ctypes.byref(count),
+                                    ctypes.byref(kwin), ctypes.byref(delta)) == 0
+    recs = [tuple(buf[7 * i:7 * i + 7]) for i in range(count.value)]
+    return recs, kwin.value, delta.value
 
 
 def schedule(lo, hi, npairs, nbc_req):
-    nbc = max(1, min(nbc_req, npairs, MAX_BULGES))
-    nbc = max(nbc, (npairs + MAX_CHAINS - 1) // MAX_CHAINS)
-    kwin = min(KWIN_MAX, max(6 * nbc, 48))
-    delta = kwin - 3 * nbc - 1
-    if delta < 1:
-        kwin, delta = 3 * nbc + 2, 1
-    nchain = (npairs + nbc - 1) // nbc
-    S = (kwin + delta + 3 * nbc + 2 + delta - 1) // delta
-    nbs = [min(nbc, npairs - c * nbc) for c in range(nchain)]
-    tend = [(hi - lo - 1) + 3 * (nbs[c] - 1) for c in range(nchain)]
-    last = max(c * S + (tend[c] + delta) // delta for c in range(nchain))
-    for s in range(last):
-        for c in range(nchain):
-            if s < c * S:
-                continue
-            tau0 = (s - c * S) * delta
-            if tau0 > tend[c]:
-                continue
-            tau1 = min(tau0 + delta, tend[c] + 1)
-            nb = nbs[c]
-            kmin, kmax = max(lo, lo + tau0 - 3 * (nb - 1)), min(hi - 1, lo + tau1 - 1)
-            if kmin > kmax:
-                continue
-            ws = lo if kmin == lo else kmin - 1
-            we = min(kmax + 3, hi)
-            yield ws, we, tau0, tau1, nb, delta
+    recs, kwin, delta = library_schedule(lo, hi, npairs, nbc_req)
+    for s, ws, we, tau0, tau1, pair0, nb in recs:
+        yield ws, we, tau0, tau1, nb, delta
+
+
+@pytest.mark.parametrize("n,npairs,nbc,lo", [(300, 8, 4, 0), (400, 30, 10, 7), (260, 4, 1, 0), (500, 64, 32, 0),
+                                              (700, 48, 24, 3), (20000, 64, 16, 0), (5000, 1024, 0, 0)])
+def test_schedule_moves_every_bulge_through_every_row_once(n, npairs, nbc, lo):
+    """Sec. 2.3: each bulge is introduced at the top of the active block and
+    chased off its bottom: bulge j of a chain sits at row lo + tau - 3 j at
+    chain-local step tau, and every row k in [lo, hi - 1] is visited once,
+    inside the window of the launch that moves it; chains share no launch
+    window rows; every pair is used."""
+    hi = n - 1
+    recs, kwin, delta = library_schedule(lo, hi, npairs, nbc)
+    seen = {}
+    by_launch = {}
+    for s, ws, we, tau0, tau1, pair0, nb in recs:
+        assert we - ws + 1 <= kwin and 1 <= tau1 - tau0 <= delta
+        by_launch.setdefault(s, []).append((ws, we))
+        for tau in range(tau0, tau1):
+            for j in range(nb):
+                k = lo + tau - 3 * j
+                if lo <= k <= hi - 1:
+                    key = (pair0 + j, k)
+                    assert key not in seen, key
+                    seen[key] = s
+                    assert ws <= k and k + min(3, hi - k + 1) - 1 <= we
+                    if k > lo:
+                        assert ws <= k - 1
+    assert len(seen) == npairs * (hi - lo)
+    for wins in by_launch.values():
+        wins.sort()
+        for (a0, b0), (a1, b1) in zip(wins, wins[1:]):
+            assert b0 < a1
 
 
 def pattern(lo, hi, ws, we, tau0, tau1, nb):
@@ -131,35 +162,13 @@ def test_chase_u_row_ranges_numeric():
 
 
 def launches(lo, hi, npairs, nbc_req):
-    """The windows of each chase launch of a sweep: {launch: [(ws, we), ...]}
-    (same schedule as ``schedule``, grouped by launch)."""
-    nbc = max(1, min(nbc_req, npairs, MAX_BULGES))
-    nbc = max(nbc, (npairs + MAX_CHAINS - 1) // MAX_CHAINS)
-    kwin = min(KWIN_MAX, max(6 * nbc, 48))
-    delta = kwin - 3 * nbc - 1
-    if delta < 1:
-        kwin, delta = 3 * nbc + 2, 1
-    nchain = (npairs + nbc - 1) // nbc
-    S = (kwin + delta + 3 * nbc + 2 + delta - 1) // delta
-    nbs = [min(nbc, npairs - c * nbc) for c in range(nchain)]
-    tend = [(hi - lo - 1) + 3 * (nbs[c] - 1) for c in range(nchain)]
-    last = max(c * S + (tend[c] + delta) // delta for c in range(nchain))
-    out = []
-    for s in range(last):
-        wins = []
-        for c in range(nchain):
-            if s < c * S:
-                continue
-            tau0 = (s - c * S) * delta
-            if tau0 > tend[c]:
-                continue
-            tau1 = min(tau0 + delta, tend[c] + 1)
-            kmin, kmax = max(lo, lo + tau0 - 3 * (nbs[c] - 1)), min(hi - 1, lo + tau1 - 1)
-            if kmin > kmax:
-                continue
-            wins.append((lo if kmin == lo else kmin - 1, min(kmax + 3, hi)))
-        out.append(wins)
-    return out
+    """The windows of each chase launch of a sweep: [[(ws, we), ...], ...]
+    in launch order, from the library's schedule."""
+    recs, _, _ = library_schedule(lo, hi, npairs, nbc_req)
+    out = {}
+    for s, ws, we, *_ in recs:
+        out.setdefault(s, []).append((ws, we))
+    return [out[s] for s in sorted(out)]
 
 
 @pytest.mark.parametrize("n,npairs,nbc,lo", [(20000, 64, 16, 0), (5000, 32, 16, 37), (3000, 32, 8, 0),

@@ -45,6 +45,8 @@ SCALAR_CASES = [
      {0: [2, -1], 1: [None], 2: [0], 3: [-1], 4: [-1], 5: [-1], 6: [0, 1025], 7: [None], 8: [3]}),
     ("schur_fastmath_eval", [N, DEV, DEV],
      {0: [-1], 1: [None], 2: [None]}),
+    ("schur_chase_schedule", [0, 100, 8, 4, 4, (ctypes.c_int * 28)(), ctypes.byref(ctypes.c_int()), None, None],
+     {0: [-1], 1: [1, -5], 2: [0, 1025], 3: [-1], 4: [-1], 5: [None], 6: [None]}),
     ("schur_vigilant_eval", [N, DEV, 0, 0.0, 1.0, 4, DEV],
      {0: [-1], 1: [None], 2: [-1, 3], 5: [0], 6: [None]}),
     ("schur_spike_eval", [N, DEV, 0, 0.0, 1.0, 4, DEV],
@@ -56,7 +58,7 @@ SCALAR_CASES = [
 def test_scalar_entry_points_reject_each_bad_argument(name, args, bad):
     lib = _lib.load()
     fn = getattr(lib, name)
-    full = list(args) + [_opts()]
+    full = list(args) + ([_opts()] if len(fn.argtypes) > len(args) else [])
     for i, values in bad.items():
         for v in values:
             _expect(fn, full, i, v)
