@@ -19,18 +19,20 @@ scales it cubically to n = 20000.
 """
 
 import argparse
+import ctypes
 import json
+import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-
-FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12   # TFLOP/s: SMs x FP64 FMA/clk x 2 x max clock
 
 
 def parse():
@@ -47,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the batched (4096 x n in [32,768]) and backward (256 x n in [64,1024]) metrics")
+    ap.add_argument("--no-checks", action="store_true", help="skip the full-size checks of the last reduction")
+    ap.add_argument("--no-cpu-lapack", action="store_true", help="skip the LAPACK (scipy.linalg.schur) CPU sample")
     return ap.parse_args()
 
 
@@ -246,6 +250,168 @@ def secondary_metrics(api, inputs, torch, np):
     return out
 
 
+# DRAM traffic of k_apply_u from one ncu capture (profiles/ncu_apply_u_n5000.md:
+# dram__bytes_read.sum + dram__bytes_write.sum over the captured launches,
+# divided by the flops those launches execute), valid for the kernel source
+# whose hash is recorded; scaled to an average launch of the benchmark by its
+# executed flops.
+APPLY_U_CAPTURE = {"sha": "bb05e315c431c5f3", "dram_bytes_per_exec_flop": 7.862e6 / (2184192 * 64),
+                   "case": "n=5000 hess_n, 64 shifts, window 128; 3 launches of k_apply_u<64> after 300"}
+
+
+def apply_u_source_hash():
+    """Hash of k_apply_u's source (the part of kernels.cu from the product
+    kernel's comment to its launcher)."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2007_03576_gb300", "csrc", "kernels.cu")).read()
+    a = src.find("// Off-window products (Sec. 3.2.1 left/right update)")
+    b = src.find("cudaError_t launch_apply_u(")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16] if a >= 0 and b > a else None
+
+
+def apply_u_traffic(exec_flops_per_launch):
+    """DRAM bytes of an average k_apply_u launch, from the capture above; None
+    when there is no capture of the current kernel source."""
+    cap = APPLY_U_CAPTURE
+    if not cap or not exec_flops_per_launch or cap["sha"] != apply_u_source_hash():
+        return None
+    return cap["dram_bytes_per_exec_flop"] * exec_flops_per_launch
+
+
+def host_cpu():
+    """CPU model and the number of host cores (for the CPU baselines)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+
+
+def lapack_schur_sample():
+    """LAPACK's real Schur factorisation (scipy.linalg.schur = dgees, OpenBLAS
+    on all host cores) of the n = 256 and n = 4096 hess_n workloads: a tuned
+    CPU library beside the plain oracle (not the method's code path)."""
+    code = (
+        "import sys, time, json\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import scipy, scipy.linalg\n"
+        "from paper_2007_03576_gb300 import inputs\n"
+        "out = {}\n"
+        "for n, seed in ((256, 2020), (4096, 2021)):\n"
+        "    H = inputs.hessrand(n, seed)\n"
+        "    t = time.perf_counter()\n"
+        "    scipy.linalg.schur(H, overwrite_a=True, check_finite=False)\n"
+        "    out[str(n)] = time.perf_counter() - t\n"
+        "out['scipy'] = scipy.__version__\n"
+        "print(json.dumps(out))\n"
+    )
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=1800)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def fp64_peaks(api, _lib, torch, local):
+    """In-run FP64 rates: the library's FMA throughput probe (the products'
+    instruction; the roofline denominator) with clocks sampled while it runs,
+    and cuBLAS DGEMM 8192^3 (a library run, for reference)."""
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    blocks = 8 * nsm
+    out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    o = _lib.make_opts(stream.cuda_stream)
+    flops = ctypes.c_double()
+    lib = _lib.load()
+
+    def probe(iters):
+        assert lib.schur_fp64_fma_probe(iters, blocks, out.data_ptr(), ctypes.byref(flops), ctypes.byref(o)) == 0
+        return flops.value
+
+    probe(2000)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    rates = []
+    for _ in range(8):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f = probe(60000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rates.append(f / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    clocks = sampler.stop()
+    a = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    b = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    a @ b
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record()
+    for _ in range(3):
+        a @ b
+    g1.record()
+    torch.cuda.synchronize()
+    dgemm = 3 * 2 * 8192 ** 3 / (g0.elapsed_time(g1) / 1e3) / 1e12
+    del a, b
+    return {"fma_probe_tflops": max(rates), "fma_probe_median_tflops": statistics.median(rates),
+            "fma_probe_clocks": clocks, "dgemm_tflops": dgemm,
+            "fma_probe": f"{blocks} blocks x 256 threads x 8 FMA chains, best of 8 launches, CUDA events"}
+
+
+def full_checks(torch, np, H0, S, Z, wr, wi, n, seed):
+    """Checks of the last reduction at full size (after the timed region):
+    backward error ||H Z - Z S||_F / ||H||_F and ||Z^T Z - I||_F / sqrt(n)
+    (Sec. 5.4) with cuBLAS products, the standardised quasi-triangular
+    structure of S and its agreement with wr/wi, and, when a stored LAPACK
+    spectrum of this matrix exists, a one-to-one nearest matching of the
+    eigenvalues to it."""
+    out = {}
+    nh = float(torch.linalg.matrix_norm(H0))
+    R = H0 @ Z
+    R -= Z @ S
+    out["residual_fro"] = float(torch.linalg.matrix_norm(R)) / nh
+    del R
+    G = Z.t() @ Z
+    G.diagonal().sub_(1.0)
+    out["orthogonality_fro_over_sqrt_n"] = float(torch.linalg.matrix_norm(G)) / math.sqrt(n)
+    del G
+    torch.cuda.empty_cache()
+    below = float(torch.tril(S, -2).abs().max()) if n > 2 else 0.0
+    sub = torch.diagonal(S, -1)
+    nz = sub != 0
+    adjacent = int((nz[1:] & nz[:-1]).sum()) if n > 2 else 0
+    d = torch.diagonal(S)
+    sup = torch.diagonal(S, 1)
+    j = torch.nonzero(nz).flatten()
+    eqdiag = int((d[j] != d[j + 1]).sum())
+    sign = int((sup[j] * sub[j] >= 0).sum())
+    wi_bad = int(((wi[j] <= 0) | (wi[j + 1] >= 0)).sum())
+    out["structure_errors"] = {"below_subdiagonal_max": below, "adjacent_subdiagonals": adjacent,
+                               "unequal_block_diagonal": eqdiag, "block_offdiag_sign": sign,
+                               "wi_pairing": wi_bad, "blocks_2x2": int(j.numel())}
+    out["structure_ok"] = below == 0.0 and adjacent == 0 and eqdiag == 0 and sign == 0 and wi_bad == 0
+    path = os.path.join(ROOT, "tests", "golden", f"hess_n{n}_seed{seed}_eigvals.npy")
+    if os.path.exists(path):
+        from scipy.spatial import cKDTree
+        ref = np.load(path)
+        lam = wr.cpu().numpy() + 1j * wi.cpu().numpy()
+        tree = cKDTree(np.stack([ref.real, ref.imag], axis=1))
+        dist, idx = tree.query(np.stack([lam.real, lam.imag], axis=1))
+        one_to_one = len(np.unique(idx)) == n
+        hf = nh
+        out["lapack_eigs"] = {"max_dist_over_normH": float(np.max(dist)) / hf,
+                              "median_dist_over_normH": float(np.median(dist)) / hf,
+                              "one_to_one": bool(one_to_one),
+                              "within_1e-10_normH": int(np.sum(dist <= 1e-10 * hf)),
+                              "reference": os.path.relpath(path, ROOT)}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -255,7 +421,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2007_03576_gb300 import api, inputs, _lib
+    from paper_2007_03576_gb300 import api, inputs, _lib, trace
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -288,7 +454,6 @@ def main():
 
     o_plain = opts(0)
     o_timed = opts(1)
-
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float64, device="cuda") if needs_flush(n) else None
 
     def step(o):
@@ -299,9 +464,19 @@ def main():
         if rc != 0:
             raise RuntimeError(f"schur_hessenberg returned {rc}: {_lib.status(rc)}")
 
-    for _ in range(args.warmup):
-        step(o_plain)
+    # warm-up; the last warm-up step writes the timeline of its launches
+    # (SCHUR_TRACE) for the union of the products' intervals
+    trace_path = os.path.join(tempfile.gettempdir(), f"schur_bench_trace_{os.getpid()}.csv")
+    for w in range(args.warmup):
+        if w == args.warmup - 1:
+            os.environ["SCHUR_TRACE"] = trace_path
+        step(o_timed if w == args.warmup - 1 else o_plain)
+        os.environ.pop("SCHUR_TRACE", None)
     torch.cuda.synchronize()
+    traced_stats = api.last_stats()
+    tsum = trace.summarize(trace_path) if os.path.exists(trace_path) else None
+    if os.path.exists(trace_path):
+        os.remove(trace_path)
 
     # timed region: K steps, CUDA events on the launching stream; the library
     # records per-phase CUDA events (timing=1) for the roofline of k_apply_u
@@ -326,12 +501,8 @@ def main():
         dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
     ms = float(t_step.item())
 
-    # correctness probe of the last step (cheap, O(n^2)): trace invariant,
-    # residual and orthogonality along a random vector
-    x = torch.randn(n, dtype=torch.float64, device="cuda")
-    resid = float(((Z @ (H @ (Z.t() @ x))) - H0 @ x).norm() / (torch.linalg.matrix_norm(H0) * x.norm()))
-    orth = float((Z.t() @ (Z @ x) - x).norm() / x.norm())
-    trace_err = abs(float(wr.sum()) - float(torch.diagonal(H0).sum())) / float(torch.diagonal(H0).abs().sum())
+    # checks of the last step at full size (outside the timed region)
+    checks = None if args.no_checks else full_checks(torch, np, H0, H, Z, wr, wi, n, args.seed + rank)
 
     # end to end: pinned host input, host->device copy, reduction, device->host
     # copy of the result (S, Z, eigenvalues), all inside the timed region
@@ -361,35 +532,30 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e = {"value": float(t.item()) / world, "unit": "s", "h2d_bytes_per_step": n * n * 8,
                "d2h_bytes_per_step": 2 * n * n * 8 + 2 * n * 8, "steps": 1}
+        del Hh, Sh, Zh, wh
 
-    # in-run FP64 GEMM reference (cuBLAS DGEMM through torch, a library run
-    # used only as a denominator)
-    a = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
-    b = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
-    a @ b
-    torch.cuda.synchronize()
-    g0 = torch.cuda.Event(enable_timing=True)
-    g1 = torch.cuda.Event(enable_timing=True)
-    g0.record()
-    for _ in range(3):
-        a @ b
-    g1.record()
-    torch.cuda.synchronize()
-    dgemm_tflops = 3 * 2 * 8192 ** 3 / (g0.elapsed_time(g1) / 1e3) / 1e12
-    del a, b
-
+    del H0
+    torch.cuda.empty_cache()
+    peaks = fp64_peaks(api, _lib, torch, local)
     sec = None if args.no_secondary else secondary_metrics(api, inputs, torch, np)
 
     st = stats[-1]
-    upd_flops = sum(s["sweep_gemm_flops"] for s in stats)
-    # kernel time of the sweep products on all three streams (H rows on the
-    # main stream, H rows above the windows on the side stream, Z on the
-    # low-priority stream); they overlap in wall time, so this is the sum of
-    # the products' own durations
+    # the dominant kernel, k_apply_u (the sweeps' off-window products on H's
+    # rows, H's columns above the windows and Z): algorithmic flops = those
+    # of applying the sweeps' 3x3 reflectors directly (12 per reflector and
+    # row/column entry); executed flops = what the banded window products
+    # compute; durations = the launches' CUDA-event times on their streams
+    alg_flops = sum(s["reflector_flops"] for s in stats)
+    exec_flops = sum(s["sweep_gemm_flops"] for s in stats)
     upd_ms = sum(s["t_update_ms"] + s["t_z_ms"] for s in stats)
     upd_launches = sum(s["update_launches"] for s in stats)
-    achieved = upd_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
+    achieved = alg_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None
+    # the larger of the two in-run FP64 rates (the FMA probe, cuBLAS DGEMM)
+    peak = max(peaks["fma_probe_tflops"], peaks["dgemm_tflops"])
+    union_ms = tsum["union_ms"]["products"] if tsum else None
+    achieved_union = (traced_stats["reflector_flops"] / (union_ms / 1e3) / 1e12) if union_ms else None
     launches = int(sum(s["kernel_launches"] for s in stats) / len(stats))
+    traffic = apply_u_traffic(upd_launches and (exec_flops / upd_launches))
 
     if rank != 0:
         return
@@ -399,7 +565,15 @@ def main():
         t = cpu_baseline_sample(n_sample, args.seed)
         cpu = {"value": t * (n / n_sample) ** 3, "unit": "s", "cores": 1, "kind": "oracle",
                "sample": f"oracle (numpy FP64, 1 thread) on one n={n_sample} hess_n reduction: {t:.2f} s, "
-                         f"scaled by (n/{n_sample})^3"}
+                         f"scaled by (n/{n_sample})^3", **host_cpu()}
+        if not args.no_cpu_lapack:
+            lap = lapack_schur_sample()
+            cpu["lapack_schur_s"] = {k: v for k, v in lap.items() if k != "scipy"}
+            cpu["lapack_note"] = (f"scipy {lap.get('scipy')} linalg.schur (LAPACK dgees via OpenBLAS, all "
+                                  f"{os.cpu_count()} host cores) on hess_n n=256 (seed 2020) and n=4096 (seed 2021)")
+            ref = os.path.join(ROOT, "tests", "golden", f"hess_n{n}_seed{args.seed}_eigvals.json")
+            if os.path.exists(ref):
+                cpu["lapack_offline"] = json.loads(open(ref).read())
     phase_ms = {k: round(st[k], 1)
                 for k in ("t_chase_ms", "t_update_ms", "t_z_ms", "t_aed_ms", "t_aed_update_ms", "t_small_ms")}
     line = {
@@ -416,23 +590,34 @@ def main():
         "dtype": "f64",
         "data": "synthetic",
         "config": bench_config(args, world),
-        "roofline": {"bound": "alu", "kernel": "k_apply_u (off-window products, FP64 FFMA)",
-                     "achieved": achieved, "peak": FP64_PEAK_DERIVED, "unit": "TFLOP/s",
-                     "frac": (achieved / FP64_PEAK_DERIVED) if achieved else None, "traffic": None,
-                     "peak_note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                     "dgemm_tflops_same_run": dgemm_tflops,
-                     "frac_of_dgemm": (achieved / dgemm_tflops) if achieved else None,
-                     "launches": upd_launches, "flops": upd_flops, "ms": upd_ms},
+        "roofline": {"bound": "alu", "kernel": "k_apply_u (off-window products of the sweeps, FP64 FMA)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "peak_note": "measured in this run: max of the library's FP64 FMA probe "
+                                  "(schur_fp64_fma_probe, clocks in peaks.fma_probe_clocks) and cuBLAS DGEMM 8192^3",
+                     "achieved_note": "algorithmic flops (3x3 reflectors applied directly, 12 per entry) / "
+                                      "sum of the launches' CUDA-event durations",
+                     "achieved_union": achieved_union,
+                     "frac_union": (achieved_union / peak) if achieved_union else None,
+                     "union_note": "algorithmic flops / union of the products' intervals on the three streams "
+                                   "(last warm-up step, SCHUR_TRACE)",
+                     "executed_flops": exec_flops, "algorithmic_flops": alg_flops,
+                     "executed_over_algorithmic": exec_flops / alg_flops if alg_flops else None,
+                     "executed_tflops": exec_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else None,
+                     "launches": upd_launches, "ms": upd_ms, "union_ms": union_ms},
+        "peaks": peaks,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": launches,
         "phase_ms": phase_ms,
+        "timeline": ({k: round(v, 1) for k, v in tsum["union_ms"].items()} | {"span": round(tsum["span_ms"], 1)})
+        if tsum else None,
         "iterations": {"aed": st["aed_steps"], "sweeps": st["sweeps"], "deflated_by_aed": st["deflated_by_aed"]},
         "flops": {"reflector_algorithmic": st["reflector_flops"], "sweep_gemm_executed": st["sweep_gemm_flops"],
                   "aed_gemm_executed": st["aed_gemm_flops"]},
         "secondary": sec,
-        "check": {"residual_probe": resid, "orthogonality_probe": orth, "trace_rel_err": trace_err},
+        "check": checks,
         "context": "paper Table 4: syn_20000 StarNEig 68 s on 25 Skylake cores (different matrix family)",
     }
     print(json.dumps(line), flush=True)

@@ -314,6 +314,22 @@ int schur_apply_u(int side, double* A, int lda, int r0, int c0, int m, int k, co
 int schur_fastmath_eval(int n, const double* x, double* out, const schur_opts* opts);
 
 /*
+ * schur_fp64_fma_probe -- FP64 fused multiply-add throughput of this GPU
+ * (not in the paper; the denominator of the off-window products' roofline,
+ * which execute FP64 FMAs).  Launches `blocks` blocks of 256 threads, each
+ * thread running 8 independent dependent chains of `iters` FMAs, on
+ * opts->stream WITHOUT synchronising: the caller times it with events on
+ * that stream.
+ *   iters   >= 1                                                       (arg 1)
+ *   blocks  >= 1 (a multiple of the SM count fills the GPU)             (arg 2)
+ *   out     device, blocks * 256 doubles (results, keeps the work)      (arg 3)
+ *   flops   host (output): the FP64 flops the launch executes (2 per FMA)
+ *                                                                       (arg 4)
+ *   opts    may be NULL (stream)                                        (arg 5)
+ */
+int schur_fp64_fma_probe(int iters, int blocks, double* out, double* flops, const schur_opts* opts);
+
+/*
  * schur_chase_schedule -- the window schedule of one multishift sweep as the
  * driver issues it (Sec. 2.3 / 2.4, Fig. 3; host computation only, no
  * device work).  npairs bulges are chased in chains of at most

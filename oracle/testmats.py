@@ -45,11 +45,34 @@ def haar_orthogonal(n, rng):
     return Q * np.sign(np.diag(R))[None, :]
 
 
-def prescribed(n, rng, nonnormal=False):
+def prescribed_blocks(n, rng, nonnormal=False):
+    """(T, eigenvalues) of the prescribed-spectrum family before the
+    similarity: T = D (+ N), D block diagonal with n/2 real eigenvalues
+    ~ U[-10, 10] and n/4 blocks [[a, b], [-b, a]], a ~ U[-10, 10],
+    b ~ U[0.5, 10]; N strictly upper U[-1, 1] (non-normal variant), zero
+    inside the 2x2 blocks.  Draws the same numbers as ``prescribed``."""
+    T, lam, _ = _prescribed_parts(n, rng, nonnormal)
+    return T, lam
+
+
+def prescribed(n, rng, nonnormal=False, reduce=None):
     """(H, eigenvalues): n/2 real eigenvalues ~ U[-10, 10] and n/4 complex
     pairs a +- i b, a ~ U[-10, 10], b ~ U[0.5, 10] as 2x2 blocks
     [[a, b], [-b, a]]; optional strictly upper U[-1, 1] part (non-normal);
-    A = Q D Q^T with Haar Q, then Householder-reduced to Hessenberg form."""
+    A = Q D Q^T with Haar Q, then reduced to Hessenberg form by Householder
+    reflectors (``reduce``: A -> H, default the oracle's unblocked
+    reduction; any orthogonal reduction keeps the spectrum)."""
+    T, lam, rng = _prescribed_parts(n, rng, nonnormal)
+    Q = haar_orthogonal(n, rng)
+    A = Q @ T @ Q.T
+    if reduce is None:
+        H, _ = hessenberg_reduce(A)
+    else:
+        H = reduce(A)
+    return H, np.array(lam)
+
+
+def _prescribed_parts(n, rng, nonnormal):
     npairs = n // 4
     nreal = n - 2 * npairs
     D = np.zeros((n, n))
@@ -72,9 +95,7 @@ def prescribed(n, rng, nonnormal=False):
             j = nreal + 2 * k
             N[j, j + 1] = 0.0
         D = D + N
-    Q = haar_orthogonal(n, rng)
-    H, _ = hessenberg_reduce(Q @ D @ Q.T)
-    return H, np.array(lam)
+    return D, np.array(lam), rng
 
 
 def syn(n, rng):

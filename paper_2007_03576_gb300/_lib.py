@@ -98,6 +98,7 @@ _SIGS = {
     "schur_batched_set_table": (c_int, [c_int, P(c_int), P(c_int), P(c_int)]),
     "schur_hessenberg_noalloc": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p,
                                          P(SchurOpts)]),
+    "schur_fp64_fma_probe": (c_int, [c_int, c_int, c_void_p, P(c_double), P(SchurOpts)]),
     "schur_chase_schedule": (c_int, [c_int, c_int, c_int, c_int, c_int, c_void_p, P(c_int), P(c_int), P(c_int)]),
     "schur_vigilant_eval": (c_int, [c_int, c_void_p, c_int, c_double, c_double, c_int, c_void_p, P(SchurOpts)]),
     "schur_spike_eval": (c_int, [c_int, c_void_p, c_int, c_double, c_double, c_int, c_void_p, P(SchurOpts)]),

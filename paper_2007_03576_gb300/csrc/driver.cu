@@ -1213,3 +1213,18 @@ extern "C" int schur_chase_schedule(int lo, int hi, int npairs, int bulges_per_c
   *count = nrec;
   return SCHUR_OK;
 }
+
+// ---------------------------------------------------------------------------
+// FP64 FMA throughput probe (the roofline's in-run peak).
+// ---------------------------------------------------------------------------
+extern "C" int schur_fp64_fma_probe(int iters, int blocks, double* out, double* flops, const schur_opts* opts) {
+  if (iters < 1) return -1;
+  if (blocks < 1) return -2;
+  if (!out) return -3;
+  if (!flops) return -4;
+  schur_opts o;
+  read_opts(opts, &o);
+  if (fma_probe_launch(iters, blocks, out, (cudaStream_t)o.stream)) return SCHUR_ERR_CUDA;
+  *flops = 2.0 * 8.0 * (double)iters * 256.0 * (double)blocks;
+  return SCHUR_OK;
+}

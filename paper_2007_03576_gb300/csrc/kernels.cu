@@ -578,6 +578,32 @@ __global__ void k_extract_eigs(const double* H, long long ldh, int n, double* wr
 }
 
 // ---------------------------------------------------------------------------
+// FP64 FMA throughput probe: every thread runs FM_CHAINS independent
+// dependent chains of fused multiply-adds (the instruction the off-window
+// products execute), so every sub-partition always has an FP64 instruction
+// ready; the result is written so that nothing is optimised away.
+#define FM_CHAINS 8
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, double* out) {
+  double a[FM_CHAINS];
+#pragma unroll
+  for (int c = 0; c < FM_CHAINS; ++c) a[c] = 1.0 + 1e-9 * (threadIdx.x + c);
+  const double m = 0.9999999999, b = 1e-10;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < FM_CHAINS; ++c) a[c] = fma(a[c], m, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < FM_CHAINS; ++c) s += a[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+int fma_probe_launch(int iters, int blocks, double* out, cudaStream_t st) {
+  k_fma_probe<<<blocks, 256, 0, st>>>(iters, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+// ---------------------------------------------------------------------------
 // Diagnostics: the deflation tests of Sec. 5.6 on given data.
 __global__ void k_vigilant_eval(int count, const double* H, DeflParams dp, int* out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {

@@ -21,6 +21,7 @@ __global__ void k_chase(double* H, long long ldh, const double* pairs, double* U
 __global__ void k_extract_eigs(const double* H, long long ldh, int n, double* wr, double* wi);
 __global__ void k_set_int(int* p, int v);
 __global__ void k_fastmath_eval(int n, const double* x, double* out);
+int fma_probe_launch(int iters, int blocks, double* out, cudaStream_t st);   // 256 threads x 8 FMA chains
 __global__ void k_vigilant_eval(int count, const double* H, DeflParams dp, int* out);
 __global__ void k_spike_eval(int count, const double* blk, DeflParams dp, int* out);
 

@@ -45,6 +45,8 @@ SCALAR_CASES = [
      {0: [2, -1], 1: [None], 2: [0], 3: [-1], 4: [-1], 5: [-1], 6: [0, 1025], 7: [None], 8: [3]}),
     ("schur_fastmath_eval", [N, DEV, DEV],
      {0: [-1], 1: [None], 2: [None]}),
+    ("schur_fp64_fma_probe", [100, 4, DEV, ctypes.byref(ctypes.c_double())],
+     {0: [0], 1: [0], 2: [None], 3: [None]}),
     ("schur_chase_schedule", [0, 100, 8, 4, 4, (ctypes.c_int * 28)(), ctypes.byref(ctypes.c_int()), None, None],
      {0: [-1], 1: [1, -5], 2: [0, 1025], 3: [-1], 4: [-1], 5: [None], 6: [None]}),
     ("schur_vigilant_eval", [N, DEV, 0, 0.0, 1.0, 4, DEV],
