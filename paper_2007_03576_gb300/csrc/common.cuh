@@ -22,6 +22,9 @@
 #define MAX_CHAINS 32        // bulge chains chased concurrently in one launch
 #define MAX_BULGES_PER_CHAIN 32
 #define MAX_UPD_TASKS (3 * MAX_CHAINS + 4)
+// doubles per chase window in the U buffers: U (kwin x kwin) followed by the
+// row range of U's nonzeros in each column (kwin int2)
+#define CHASE_USLOT(kwin) ((kwin) * (kwin) + (kwin))
 
 struct DeflParams {
   int mode;        // 0 lapack, 1 norm, 2 fixed
@@ -78,6 +81,8 @@ struct UpdTask {
   int ntile;
   const int* gate;  // optional: skip when *gate == 0 (e.g. AED deflated nothing)
   int lbw, ubw;     // U[k, i] = 0 when k - i > lbw or i - k > ubw (L = dense)
+  const int2* rng;  // optional (device): U[k, i] = 0 unless rng[i].x <= k <= rng[i].y
+  const int2* hrng; // the same ranges on the host (executed-flop count); nullptr = none
 };
 
 struct UpdArgs {

@@ -74,7 +74,7 @@ struct LevelSizes {
   size_t bytes() const {
     size_t b = 0;
     b += align_up(sizeof(Ctl));
-    b += align_up((size_t)MAX_CHAINS * KWIN_MAX * KWIN_MAX * sizeof(double));  // chase U
+    b += align_up((size_t)MAX_CHAINS * CHASE_USLOT(KWIN_MAX) * sizeof(double));  // chase U + column ranges
     b += align_up((size_t)nwmax * nwmax * sizeof(double));                       // V
     b += align_up(arena * sizeof(double));
     b += (nwmax > fmax) ? align_up((size_t)nwmax * nwmax * sizeof(double)) : 0;  // T
@@ -112,9 +112,9 @@ static void level_plan(int n, const schur_opts& o, std::vector<LevelSizes>& out)
       int delta = std::max(1, kwin - 3 * nbc - 1);
       size_t nchain = (size_t)std::max(1, (ns / 2 + nbc - 1) / nbc);
       size_t steps = (size_t)m / delta + 3 * nchain * ((size_t)(2 * kwin + 4 * nbc) / delta + 2) + 8;
-      arena = (nchain * steps + 2) * (size_t)kwin * kwin + 2 * (size_t)nw * nw;
+      arena = (nchain * steps + 2) * (size_t)CHASE_USLOT(kwin) + 2 * (size_t)nw * nw;
       arena = std::min(arena, (size_t)(1ull << 27));                       // at most 1 GiB
-      arena = std::max(arena, (size_t)MAX_CHAINS * KWIN_MAX * KWIN_MAX + (size_t)nw * nw);
+      arena = std::max(arena, (size_t)MAX_CHAINS * CHASE_USLOT(KWIN_MAX) + (size_t)nw * nw);
     }
     LevelSizes L{m, nw, ns, arena, lev == 0 ? window_francis_max(o) : NW_SMEM_MAX};
     out.push_back(L);
@@ -148,7 +148,7 @@ void Solver::carve(char* base, int n) {
     v.nwmax = L.nwmax;
     v.nsmax = L.nsmax;
     v.ctl = (Ctl*)take(sizeof(Ctl));
-    v.ubuf = (double*)take((size_t)MAX_CHAINS * KWIN_MAX * KWIN_MAX * sizeof(double));
+    v.ubuf = (double*)take((size_t)MAX_CHAINS * CHASE_USLOT(KWIN_MAX) * sizeof(double));
     v.V = (double*)take((size_t)L.nwmax * L.nwmax * sizeof(double));
     if (L.arena) {
       arena = (double*)take(L.arena * sizeof(double));
@@ -484,6 +484,8 @@ DeflParams Solver::defl(int n) const {
   return d;
 }
 
+static double apply_u_entries(const UpdTask& q, int tn);
+
 // Issue a list of off-window products (split in launches of at most
 // MAX_UPD_TASKS tasks; tasks within a launch must not overlap).
 void Solver::run_updates(std::vector<UpdTask>& tasks, cudaStream_t sarg, bool on_z) {
@@ -513,16 +515,10 @@ void Solver::run_updates(std::vector<UpdTask>& tasks, cudaStream_t sarg, bool on
       a.t[t].ntile = (a.t[t].nvec + tn - 1) / tn;
       tile += a.t[t].ntile;
       // flops the kernel executes: (row block, 16 k) tiles outside the band
-      // are skipped exactly as in k_apply_u
+      // are skipped, and inside a kept tile each warp skips the k outside
+      // the union of its rows' ranges, exactly as in k_apply_u
       const UpdTask& q = a.t[t];
-      double entries = 0.0;
-      for (int r0 = 0; r0 < q.L; r0 += RG)
-        for (int k0 = 0; k0 < q.L; k0 += 16) {
-          int r1 = std::min(q.L, r0 + RG) - 1, k1 = std::min(q.L, k0 + 16) - 1;
-          bool skip = (k0 - (r0 + RG - 1) > q.lbw) || (r0 - k1 > q.ubw);
-          if (!skip) entries += (double)(r1 - r0 + 1) * (k1 - k0 + 1);
-        }
-      if (cur_flops) *cur_flops += 2.0 * entries * q.nvec;
+      if (cur_flops) *cur_flops += 2.0 * apply_u_entries(q, tn) * q.nvec;
     }
     size_t smem = apply_u_smem_bytes(tn, maxL);
     // one tile per block: blocks stay short (~0.3 ms), so that when the two
@@ -539,6 +535,35 @@ void Solver::run_updates(std::vector<UpdTask>& tasks, cudaStream_t sarg, bool on
     tm.end(s, tok);
     if (cur_update_phase == PH_UPDATE && timer.depth == 0 && count_launches) g_stats.update_launches += 1;
   }
+}
+
+// Entries of U (row k, output row i) that k_apply_u multiplies for one
+// vector of task q at tn vectors per tile (its skip rules mirrored).
+static double apply_u_entries(const UpdTask& q, int tn) {
+  const int VG = tn / 4, RG = CTA_THREADS / VG, rows_per_warp = 32 / VG;
+  double entries = 0.0;
+  for (int r0 = 0; r0 < q.L; r0 += RG)
+    for (int k0 = 0; k0 < q.L; k0 += 16) {
+      const int k1 = std::min(q.L, k0 + 16) - 1;
+      const bool skip = (k0 - (r0 + RG - 1) > q.lbw) || (r0 - k1 > q.ubw);
+      if (skip) continue;
+      // warps of the row block: rows r0 + w * rows_per_warp .. + rows_per_warp - 1
+      for (int w0 = r0; w0 < std::min(q.L, r0 + RG); w0 += rows_per_warp) {
+        const int w1 = std::min(q.L, w0 + rows_per_warp) - 1;
+        int lo = 0, hi = q.L - 1;
+        if (q.hrng) {
+          lo = q.L;
+          hi = -1;
+          for (int i = w0; i <= w1; ++i) {
+            lo = std::min(lo, q.hrng[i].x);
+            hi = std::max(hi, q.hrng[i].y);
+          }
+        }
+        const int ka = std::max(k0, lo), kb = std::min(k1, hi);
+        if (kb >= ka) entries += (double)(w1 - w0 + 1) * (kb - ka + 1);
+      }
+    }
+  return entries;
 }
 
 static UpdTask make_task(double* A, long long lda, int side, int r0, int c0, int L, int nvec, const double* U, int ldu,
@@ -593,6 +618,28 @@ void Solver::apply_block_transform(const Mat3& M, int k0, int L, const double* U
 // ---------------------------------------------------------------------------
 // One multishift sweep (Sec. 2.3) on [lo, hi] with npairs pairs (device).
 // ---------------------------------------------------------------------------
+// Row range of the nonzeros in each column of one chase window's U (U starts
+// as I; a reflector on columns kl..kl+nr-1 gives all of them the union of
+// their ranges): the chase kernel's own bookkeeping, replayed on the host to
+// count the products' executed flops.  It depends on the schedule only.
+static void chase_u_ranges(int lo, int hi, int ws, int we, int tau0, int tau1, int nb, std::vector<int2>& r) {
+  const int L = we - ws + 1;
+  r.resize(L);
+  for (int c = 0; c < L; ++c) r[c] = make_int2(c, c);
+  for (int tau = tau0; tau < tau1; ++tau)
+    for (int j = 0; j < nb; ++j) {
+      const int k = lo + tau - 3 * j;
+      if (k < lo || k > hi - 1) continue;
+      const int nr = std::min(3, hi - k + 1), kl = k - ws;
+      int a = r[kl].x, b = r[kl].y;
+      for (int t = 1; t < nr; ++t) {
+        a = std::min(a, r[kl + t].x);
+        b = std::max(b, r[kl + t].y);
+      }
+      for (int t = 0; t < nr; ++t) r[kl + t] = make_int2(a, b);
+    }
+}
+
 // The window schedule of one sweep (Sec. 2.3 / 2.4, Fig. 3): npairs bulges
 // in chains of at most nbc; chain c starts S launches after chain c-1 so that
 // its window stays clear of the chain ahead; in every launch each chain in
@@ -633,7 +680,8 @@ static SweepPlan plan_sweep(int lo, int hi, int npairs, int nbc) {
 }
 
 // The chains of launch s (chains in order 0 = ahead, lowest); returns their
-// number (<= MAX_CHAINS); each window's U is at uoff = i * kwin^2.
+// number (<= MAX_CHAINS); window i's U is at uoff = i * CHASE_USLOT(kwin),
+// its column ranges kwin^2 doubles further.
 static int chase_launch(const SweepPlan& P, int lo, int hi, int s, ChaseArgs& a) {
   memset(&a, 0, sizeof(a));
   a.lo = lo;
@@ -656,7 +704,7 @@ static int chase_launch(const SweepPlan& P, int lo, int hi, int s, ChaseArgs& a)
     d.tau1 = tau1;
     d.pair0 = c * P.nbc;
     d.nb = nb;
-    d.uoff = na * P.kwin * P.kwin;
+    d.uoff = na * CHASE_USLOT(P.kwin);
     ++na;
   }
   a.nchain = na;
@@ -679,7 +727,7 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
     if (na == 0) continue;
     // this step's window transforms: from the arena while the Z or the side
     // stream may still need them, else the level's buffer
-    const size_t need = (size_t)na * kwin * kwin;
+    const size_t need = (size_t)na * CHASE_USLOT(kwin);
     double* ubase = use_arena ? arena_alloc(need) : Lv.ubuf;
     int tok = timer.begin(st, PH_CHASE);
     ++g_stats.kernel_launches;
@@ -694,18 +742,29 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
       const ChainDesc& d = a.c[i];
       int L = d.we - d.ws + 1;
       const double* U = ubase + d.uoff;
+      const int2* rng = (const int2*)(U + (size_t)kwin * kwin);
+      host_ranges.emplace_back();
+      chase_u_ranges(lo, hi, d.ws, d.we, d.tau0, d.tau1, d.nb, host_ranges.back());
+      const int2* hrng = host_ranges.back().data();
+      auto ranged = [&](UpdTask& t) {
+        t.rng = rng;
+        t.hrng = hrng;
+      };
       if (d.we + 1 < M.n) {
         t1.push_back(make_task(M.H, M.ldh, 0, d.ws, d.we + 1, L, M.n - d.we - 1, U, kwin, nullptr));
         set_chase_band(t1.back(), d.nb, delta);
+        ranged(t1.back());
       }
       if (M.Z) {
         std::vector<UpdTask>& tzv = zasync ? tz : t1;
         tzv.push_back(make_task(M.Z, M.ldz, 1, 0, d.ws, L, M.zrows, U, kwin, nullptr));
         set_chase_band(tzv.back(), d.nb, delta);
+        ranged(tzv.back());
       }
       if (d.ws > 0) {
         t2.push_back(make_task(M.H, M.ldh, 1, 0, d.ws, L, d.ws, U, kwin, nullptr));
         set_chase_band(t2.back(), d.nb, delta);
+        ranged(t2.back());
       }
     }
     if (zasync) z_defer(tz, ubase, need);   // issued on zst at the end of the sweep
@@ -736,6 +795,7 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
     t2_pending = false;
   }
   if (zasync) z_flush();
+  host_ranges.clear();   // every task of the sweep has been issued
   if (lev == 0) {
     // algorithmic flops of applying the reflectors directly (12 flops per
     // row/column entry of each 3x3 reflector): every bulge passes rows

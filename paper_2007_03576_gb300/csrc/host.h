@@ -124,6 +124,9 @@ struct Solver {
   double* arena_alloc(size_t n);                 // waits (on st) for overlapping live regions
   void arena_release(double* p, size_t n, bool z_reader);  // after the readers were issued
   std::vector<Level> levels;
+  // host copies of the chase windows' column ranges of the current sweep
+  // (executed-flop counts of its products); cleared at the end of the sweep
+  std::deque<std::vector<int2>> host_ranges;
 
   explicit Solver(const schur_opts* o);
   ~Solver();

@@ -369,6 +369,9 @@ __global__ void __launch_bounds__(CHASE_THREADS) k_chase(double* H, long long ld
       H[(ws + i) + (long long)(ws + j) * ldh] = W(i, j);
       Uout[i + (long long)j * args.ldu] = Us(i, j);
     }
+  // the row range of U's nonzeros in each column, for the products
+  int2* Urng = (int2*)(Uout + (size_t)args.ldu * args.ldu);
+  for (int c = tid; c < L; c += nt) Urng[c] = make_int2(ulo[c], uhi[c]);
 }
 
 // ---------------------------------------------------------------------------
@@ -424,8 +427,16 @@ __device__ __forceinline__ void apply_u_k_impl(const double* sX, const double* s
     }
   }
 }
+// row blocks a whose range [klo[a], khi[a]] contains k
+__device__ __forceinline__ unsigned fine_mask(int k, const int (&klo)[8], const int (&khi)[8]) {
+  unsigned m = 0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) m |= (k >= klo[a] && k <= khi[a]) ? (1u << a) : 0u;
+  return m;
+}
+
 template <int TN>
-__global__ void __launch_bounds__(CTA_THREADS) k_apply_u(const __grid_constant__ UpdArgs args) {
+__global__ void __launch_bounds__(CTA_THREADS, 2) k_apply_u(const __grid_constant__ UpdArgs args) {
   extern __shared__ double smem[];
   constexpr int CN = 4;
   constexpr int VG = TN / CN;          // vector groups
@@ -445,6 +456,32 @@ __global__ void __launch_bounds__(CTA_THREADS) k_apply_u(const __grid_constant__
     const int nv = min(TN, t.nvec - v0);
     const int RM = (L + RG - 1) / RG;
     const int KC = apply_u_kc(L);
+    // rows k of U that can be nonzero in the output rows of this warp, per
+    // row block a: the union of the columns' ranges over the warp's rows
+    // (warp-uniform, so the per-k skip below never diverges inside a warp)
+    int klo[8], khi[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int i = rg + RG * a;
+      int lo = L, hi = -1;
+      if (a < RM && i < L) {
+        if (t.rng != nullptr) {
+          const int2 r = t.rng[i];
+          lo = r.x;
+          hi = r.y;
+        } else {
+          lo = 0;
+          hi = L - 1;
+        }
+      }
+#pragma unroll
+      for (int o = VG; o < 32; o <<= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      klo[a] = lo;
+      khi[a] = hi;
+    }
     const int LDU = L + 1;
     double* sX = smem;                       // [L][LDV]: sX[k*LDV + v]
     double* sU = smem + (size_t)L * LDV;     // [KC][LDU]: sU[kk*LDU + i]
@@ -490,9 +527,11 @@ __global__ void __launch_bounds__(CTA_THREADS) k_apply_u(const __grid_constant__
         if (act == 0) continue;
         if (kend - k16 == 16) {
 #pragma unroll 4
-          for (int kk = k16; kk < k16 + 16; ++kk) apply_u_k_impl<CN, VG>(sX, sU, kc + kk, kk, LDV, LDU, vg, rg, RG, L, act, acc);
+          for (int kk = k16; kk < k16 + 16; ++kk)
+            apply_u_k_impl<CN, VG>(sX, sU, kc + kk, kk, LDV, LDU, vg, rg, RG, L, act & fine_mask(kc + kk, klo, khi), acc);
         } else {
-          for (int kk = k16; kk < kend; ++kk) apply_u_k_impl<CN, VG>(sX, sU, kc + kk, kk, LDV, LDU, vg, rg, RG, L, act, acc);
+          for (int kk = k16; kk < kend; ++kk)
+            apply_u_k_impl<CN, VG>(sX, sU, kc + kk, kk, LDV, LDU, vg, rg, RG, L, act & fine_mask(kc + kk, klo, khi), acc);
         }
       }
     }
