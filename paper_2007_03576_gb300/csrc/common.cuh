@@ -45,6 +45,7 @@ struct Ctl {
   int swap_fail; // a reordering swap was rejected in the last AED
   int nswaps;    // swaps performed by the last AED
   long long cyc_schur, cyc_defl, cyc_hess;  // clock64 cycles of the AED sub-steps (accumulated)
+  int sync_err;  // the AED kernel's two blocks lost contact (a bounded wait ran out)
 };
 
 // One bulge chain in one launch of the chase kernel (Sec. 2.3 / 2.4: a set of

@@ -21,6 +21,123 @@ __device__ __forceinline__ int cta_tid() { return threadIdx.x; }
 __device__ __forceinline__ int cta_nt() { return blockDim.x; }
 
 // ---------------------------------------------------------------------------
+// Transform stream between the two blocks of a cluster.
+//
+// The window Schur form of AED accumulates its reflectors and rotations into
+// V, which the Francis chain never reads.  In the AED kernel block 0 reduces
+// the window and pushes every transform, in order, through distributed
+// shared memory to block 1, which keeps V in its own shared memory and
+// applies them there.  A ring of VRING_OPS slots in block 1 holds the
+// transforms; block 0 publishes how many it wrote (release store at cluster
+// scope) and block 1 how many it applied, which block 0 waits for before it
+// reuses a slot.  Every wait gives up after VRING_TIMEOUT cycles and sets
+// err; both blocks meet at a cluster barrier after the exchange, so neither
+// touches the other's shared memory after the other has left.
+// ---------------------------------------------------------------------------
+#define VRING_OPS 256
+#define VRING_TIMEOUT 4000000000LL   // SM cycles (about 2 s)
+
+struct VOp {
+  double a, b, c;   // reflector: v1, v2, tau; rotation: cs, sn
+  int k;            // first column
+  int kind;         // 2 or 3: reflector of that order; 1: rotation; 0: end
+};
+
+struct VRing {
+  VOp ops[VRING_OPS];   // consumer: the transforms
+  unsigned count;       // consumer: transforms published
+  unsigned consumed;    // producer: transforms the consumer has applied
+  unsigned pushed;      // producer: transforms pushed so far (one thread)
+  int err;              // a wait timed out
+  VRing* remote;        // the other block's ring (generic address)
+};
+
+__device__ __forceinline__ unsigned vr_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.cluster.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void vr_st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.cluster.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Called by one thread of the producer block, in transform order.
+__device__ inline void vring_push(VRing* r, double a, double b, double c, int k, int kind) {
+  const unsigned q = r->pushed;
+  r->pushed = q + 1;
+  if (r->err) return;
+  if (q >= VRING_OPS) {
+    const long long t0 = clock64();
+    while (vr_ld_acquire(&r->consumed) + VRING_OPS <= q) {
+      if (clock64() - t0 > VRING_TIMEOUT) {
+        r->err = 1;
+        return;
+      }
+    }
+  }
+  VOp* d = &r->remote->ops[q % VRING_OPS];
+  d->a = a;
+  d->b = b;
+  d->c = c;
+  d->k = k;
+  d->kind = kind;
+  vr_st_release(&r->remote->count, q + 1);
+}
+
+// The consumer block: applies the stream to the rows 0..nrows-1 of V (one
+// thread per row) until the end mark; returns 1 if a wait timed out.
+__device__ inline int vring_consume(VRing* r, const Mat& V, int nrows) {
+  __shared__ unsigned s_avail;
+  const int tid = threadIdx.x;
+  unsigned done = 0;
+  int ended = 0, timed_out = 0;
+  while (!ended) {
+    if (tid == 0) {
+      const long long t0 = clock64();
+      unsigned c;
+      while ((c = vr_ld_acquire(&r->count)) == done) {
+        if (clock64() - t0 > VRING_TIMEOUT) break;
+      }
+      s_avail = c;
+    }
+    __syncthreads();
+    const unsigned c = s_avail;
+    if (c == done) {   // timed out (uniform: every thread reads s_avail)
+      timed_out = 1;
+      break;
+    }
+    unsigned q = done;
+    for (; q < c; ++q) {
+      const VOp op = r->ops[q % VRING_OPS];
+      if (op.kind == 0) {
+        ended = 1;
+        break;
+      }
+      if (tid < nrows) {
+        double* row = &V(tid, op.k);
+        const long long ld = V.ld;
+        if (op.kind == 1) {
+          const double x = row[0], y = row[ld];
+          row[0] = op.a * x + op.b * y;
+          row[ld] = -op.b * x + op.a * y;
+        } else {
+          const double x0 = row[0], x1 = row[ld], x2 = (op.kind == 3) ? row[2 * ld] : 0.0;
+          const double s = op.c * fma(op.b, x2, fma(op.a, x1, x0));
+          row[0] = x0 - s;
+          row[ld] = fma(-s, op.a, x1);
+          if (op.kind == 3) row[2 * ld] = fma(-s, op.b, x2);
+        }
+      }
+    }
+    done = ended ? q + 1 : c;
+    __syncthreads();   // every thread is done with the slots read above
+    if (tid == 0) vr_st_release(&r->remote->consumed, done);
+  }
+  return timed_out;
+}
+
+// ---------------------------------------------------------------------------
 // Reflector of order nr (2 or 3) at rows k..k+nr-1.
 // ---------------------------------------------------------------------------
 
@@ -83,7 +200,7 @@ __device__ inline int cta_find_ktop(const Mat& H, int lo, int hi, const DeflPara
 // (rows 0..k-1) and to U's columns k, k+1 (rows 0..urows-1).
 // ---------------------------------------------------------------------------
 __device__ inline void cta_standardize_block(const Mat& T, int k, int ncols, const Mat& U, int urows,
-                                             CtaShared* sh) {
+                                             CtaShared* sh, VRing* ring = nullptr) {
   if (cta_tid() == 0) {
     double cs, sn, B[4];
     standardize2x2(T(k, k), T(k, k + 1), T(k + 1, k), T(k + 1, k + 1), cs, sn, B);
@@ -96,6 +213,7 @@ __device__ inline void cta_standardize_block(const Mat& T, int k, int ncols, con
   }
   __syncthreads();
   double cs = sh->r[0], sn = sh->r[1];
+  if (ring && cta_tid() == 128 && !(cs == 1.0 && sn == 0.0)) vring_push(ring, cs, sn, 0.0, k, 1);
   if (!(cs == 1.0 && sn == 0.0)) {
     for (int j = k + 2 + cta_tid(); j < ncols; j += cta_nt()) {
       double a = T(k, j), b = T(k + 1, j);
@@ -152,6 +270,95 @@ __device__ inline void cta_standardize_block(const Mat& T, int k, int ncols, con
 // (beta, 0, 0) below the diagonal itself.  Reflectors alternate between two
 // slots of sh->r.
 // ---------------------------------------------------------------------------
+// The next reflector of the Francis chain on the lanes of one warp.
+//
+// Each sub-partition of the SM issues one FP64 warp instruction per ~64
+// cycles whatever the number of active lanes, so a chain of scalar FP64
+// operations costs 64 cycles per instruction, even when some of them are
+// independent.  Independent operations are therefore put in different
+// lanes of the same instruction, and values move between lanes by shuffles
+// (not on the FP64 unit):
+//   - lane r (< 4) holds row r of B = T[k..k+3, k..k+2] and computes
+//     y_r = (B P)(r, 0) (3 instructions for the four rows);
+//   - x = rows 1..3 of P y: q = w^T y, x_r = y_r - (tau q) w_r (4);
+//   - house3 of x: ||x||^2 (3), a^(-1/2) by one third-order step from an
+//     integer-built seed (4, the two middle products in two lanes), then
+//     tau = 1 + |x0| r, ||x|| = a r, x1 r and x2 r in four lanes of one
+//     instruction (1), 1/tau by one third-order step from an FP32 seed formed
+//     beside the chain (3), and v1, v2 in two lanes (1).
+// 20 FP64 instructions, against ~40 for the scalar evaluation.  The result
+// is the reflector of house3 (same formulas), up to rounding.  Every lane of
+// the warp executes the same instructions; all lanes return (v1, v2, tau,
+// beta).  b0, b1, b2: this lane's row of B (lanes >= 4: anything finite).
+__device__ __forceinline__ double warp_bcast(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+__device__ __forceinline__ void warp_next_reflector(double b0, double b1, double b2, double v1, double v2, double tau,
+                                                    int nr1, double& ov1, double& ov2, double& otau, double& obeta) {
+  const int lane = threadIdx.x & 31;
+  // y = column 0 of B P
+  const double in = fma(v2, b2, fma(v1, b1, b0));
+  const double y = fma(-tau, in, b0);
+  const double y0 = warp_bcast(y, 0), y1 = warp_bcast(y, 1), y2 = warp_bcast(y, 2);
+  // x = rows 1..3 of P y (row 3 unchanged by the left product)
+  const double q = fma(v2, y2, fma(v1, y1, y0));
+  const double tq = tau * q;
+  const double w = (lane == 1) ? v1 : ((lane == 2) ? v2 : 0.0);
+  const double xl = fma(-tq, w, y);
+  const double x0 = warp_bcast(xl, 1), x1 = warp_bcast(xl, 2);
+  const double x2 = (nr1 == 3) ? warp_bcast(xl, 3) : 0.0;
+  // house3(x)
+  const bool trivial = (fm_abs_key(x1) | fm_abs_key(x2)) == 0;
+  const bool safe = fm_safe_range3(x0, x1, x2);
+  const int h0 = __double2hiint(x0);
+  const double a = fma(x0, x0, fma(x1, x1, x2 * x2));
+  const int ha = __double2hiint(a);
+  const int e = ((ha >> 20) & 0x7ff) - 1023;
+  const int k = e >> 1;
+  const float sf = fm_rsqrt_approx_f32(fm_mantissa_f32(ha, __double2loint(a), e & 1));
+  const double ys = fm_f32_to_f64_scaled(sf, -k);
+  const int e0 = ((h0 >> 20) & 0x7ff) - 1023 - k;
+  const float x0f = (e0 < -126 || (fm_abs_key(x0) == 0))
+                        ? 0.0f
+                        : __uint_as_float(((unsigned)(e0 + 127) << 23) | (((unsigned)h0 & 0xfffffu) << 3) |
+                                          ((unsigned)__double2loint(x0) >> 29));
+  const float rtf = fm_rcp_approx_f32(fmaf(x0f, sf, 1.0f));
+  const double ay = a * ys;
+  const double ee = fma(-ay, ys, 1.0);
+  // lane 0: y e; lane 1: 3/8 e + 1/2
+  const double t = fma((lane == 1) ? 0.375 : ys, ee, (lane == 1) ? 0.5 : 0.0);
+  const double ye = warp_bcast(t, 0), pp = warp_bcast(t, 1);
+  const double r = fma(ye, pp, ys);
+  const double rs = copysign(r, x0);
+  // lane 0: tau = 1 + |x0| r; lane 1: ||x|| = a r; lane 2: x1 r; lane 3: x2 r (signed)
+  const double m1 = (lane == 0) ? fabs(x0) : ((lane == 1) ? a : ((lane == 2) ? x1 : x2));
+  const double m2 = (lane <= 1) ? r : rs;
+  const double u = fma(m1, m2, (lane == 0) ? 1.0 : 0.0);
+  const double tv = warp_bcast(u, 0), nrm = warp_bcast(u, 1), xr1 = warp_bcast(u, 2), xr2 = warp_bcast(u, 3);
+  double z = fm_f32_to_f64_scaled(rtf, 0);
+  const double et = fma(-tv, z, 1.0);
+  const double pt = fma(et, et, et);
+  z = fma(z, pt, z);
+  const double vv = ((lane == 1) ? xr2 : xr1) * z;
+  ov1 = warp_bcast(vv, 0);
+  ov2 = warp_bcast(vv, 1);
+  otau = tv;
+  obeta = -copysign(nrm, x0);
+  if (trivial) {
+    ov1 = 0.0;
+    ov2 = 0.0;
+    otau = 0.0;
+    obeta = x0;
+  } else if (!safe) {
+    double sig = hypot(x1, x2);
+    double nr = hypot(x0, sig);
+    obeta = -copysign(nr, x0);
+    otau = (obeta - x0) / obeta;
+    double den = x0 - obeta;
+    ov1 = x1 / den;
+    ov2 = x2 / den;
+  }
+}
+
 __device__ __forceinline__ void refl3_apply(double* p, long long stride, int nr, double v1, double v2, double tau) {
   double a0 = p[0], a1 = p[stride], a2 = (nr == 3) ? p[2 * stride] : 0.0;
   double s = tau * fma(v2, a2, fma(v1, a1, a0));
@@ -167,13 +374,13 @@ __device__ __forceinline__ bool francis_far_warp(int warp) { return warp >= 2 &&
 __device__ __forceinline__ int francis_far_rank(int warp) { return warp - 2 - (warp > 4 ? 1 : 0); }
 
 __device__ inline void cta_double_shift_sweep(const Mat& T, int m, int l, int i, double ssum, double sprod,
-                                              const Mat& U, int urows, CtaShared* sh) {
+                                              const Mat& U, int urows, CtaShared* sh, VRing* ring = nullptr) {
   __shared__ double bnext[2][16];   // B_k for the chain lane, by step parity (row r, column c at r + 4c)
   const int tid = cta_tid(), nt = cta_nt(), lane = tid & 31, warp = tid >> 5;
   // far warps: 2..nwarps-1 without 4 (blocks of at least 3 warps; the kernels use 8)
   const int nwarps = nt >> 5;
   const int nfar = nwarps - 2 - (nwarps > 4 ? 1 : 0);
-  // chain lane state: the current reflector
+  // the chain warp's state: the current reflector (the same in every lane)
   double cv1 = 0.0, cv2 = 0.0, ctau = 0.0;
   if (tid == 0) {
     const int nr = min(3, i - l + 1);
@@ -192,36 +399,36 @@ __device__ inline void cta_double_shift_sweep(const Mat& T, int m, int l, int i,
         bnext[(l & 1)][r + 4 * c] = (l + r <= i && r <= c + 1) ? T(l + r, l + c) : 0.0;
   }
   __syncthreads();
-  const int nu = U.p ? urows : 0;
+  if (warp == 0) {   // every lane of the chain warp carries the current reflector
+    cv1 = sh->r[0];
+    cv2 = sh->r[1];
+    ctau = sh->r[2];
+  }
+  // with a transform stream the accumulation happens in the other block
+  const int nu = (U.p && !ring) ? urows : 0;
   for (int k = l; k < i; ++k) {
     const int nr = min(3, i - k + 1);
     const int slot = ((k - l) & 1) * 4;
+    if (ring && tid == 128 && sh->r[slot + 2] != 0.0)
+      vring_push(ring, sh->r[slot], sh->r[slot + 1], sh->r[slot + 2], k, nr);
     if (warp == 0) {
-      if (lane == 0 && k + 1 < i) {
-        // here nr == 3; next reflector from column k of P_k B_k P_k
+      if (k + 1 < i) {
+        // here nr == 3; the next reflector from column k of P_k B_k P_k
         const double* B = bnext[k & 1];
-        const double v1 = cv1, v2 = cv2, tau = ctau;
-        const double tv1 = tau * v1, tv2 = tau * v2;
-        double y[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const double in = fma(v2, B[r + 8], fma(v1, B[r + 4], B[r]));
-          y[r] = fma(-tau, in, B[r]);
-        }
-        const double q = fma(v2, y[2], fma(v1, y[1], y[0]));
-        const double x0 = fma(-tv1, q, y[1]);
-        const double x1 = fma(-tv2, q, y[2]);
+        const int rr = lane & 3;
+        const double b0 = B[rr], b1 = B[rr + 4], b2 = B[rr + 8];
         const int k1 = k + 1, nr1 = min(3, i - k1 + 1);
-        const double x2 = (nr1 == 3) ? y[3] : 0.0;
         double beta;
-        house3(nr1, x0, x1, x2, cv1, cv2, ctau, beta);
-        T(k1, k) = beta;
-        T(k1 + 1, k) = 0.0;
-        if (nr1 == 3) T(k1 + 2, k) = 0.0;
-        const int s1 = 4 - slot;
-        sh->r[s1] = cv1;
-        sh->r[s1 + 1] = cv2;
-        sh->r[s1 + 2] = ctau;
+        warp_next_reflector(b0, b1, b2, cv1, cv2, ctau, nr1, cv1, cv2, ctau, beta);
+        if (lane == 0) {
+          T(k1, k) = beta;
+          T(k1 + 1, k) = 0.0;
+          if (nr1 == 3) T(k1 + 2, k) = 0.0;
+          const int s1 = 4 - slot;
+          sh->r[s1] = cv1;
+          sh->r[s1 + 1] = cv2;
+          sh->r[s1 + 2] = ctau;
+        }
       }
     } else if (warp == 1) {
       const double v1 = sh->r[slot], v2 = sh->r[slot + 1], tau = sh->r[slot + 2];
@@ -324,7 +531,7 @@ __device__ __forceinline__ void exceptional_pair(const Mat& T, int lo, int i, do
 // lo..i unreduced.
 // ---------------------------------------------------------------------------
 __device__ inline int cta_francis(const Mat& T, int m, int lo, int hi, const Mat& U, int urows, const DeflParams& dp,
-                                  CtaShared* sh) {
+                                  CtaShared* sh, VRing* ring = nullptr) {
   int i = hi;
   int itmax = 30 * max(10, hi - lo + 1);
   int total = 0;
@@ -345,12 +552,12 @@ __device__ inline int cta_francis(const Mat& T, int m, int lo, int hi, const Mat
         ssum = a + d;
         sprod = a * d - b * c;
       }
-      cta_double_shift_sweep(T, m, l, i, ssum, sprod, U, urows, sh);
+      cta_double_shift_sweep(T, m, l, i, ssum, sprod, U, urows, sh, ring);
     }
     if (l == i) {
       i -= 1;
     } else {
-      cta_standardize_block(T, i - 1, m, U, urows, sh);
+      cta_standardize_block(T, i - 1, m, ring ? Mat{nullptr, 1} : U, urows, sh, ring);
       i -= 2;
     }
   }

@@ -901,7 +901,8 @@ int Solver::aed(const Mat3& M, int lev, int ktop, int kbot, int nw, int ns_max, 
   if (in_block) {
     size_t smem = (size_t)(nw | 1) * nw * sizeof(double);
     ++g_stats.kernel_launches;
-    k_aed_small<<<1, CTA_THREADS, smem, st>>>(M.H, M.ldh, ktop, kbot, nw, V, nw, Lv.cand_re, Lv.cand_im, Lv.vbuf,
+    // a cluster of two blocks: the window on one, its transform V on the other
+    k_aed_small<<<2, CTA_THREADS, smem, st>>>(M.H, M.ldh, ktop, kbot, nw, V, nw, Lv.cand_re, Lv.cand_im, Lv.vbuf,
                                              dp, dpw, Lv.ctl);
     ck(cudaGetLastError());
   } else {
@@ -927,6 +928,10 @@ int Solver::aed(const Mat3& M, int lev, int ktop, int kbot, int nw, int ns_max, 
                                  Lv.cand_im, Lv.pairs, Lv.ctl);
   ck(cudaGetLastError());
   read_ctl(Lv.ctl);
+  if (hctl->sync_err) {
+    snprintf(g_err_detail, sizeof(g_err_detail), "the AED kernel's transform stream between its two blocks timed out");
+    throw CudaError{cudaErrorLaunchTimeout};
+  }
   if (zasync) {
     if (hctl->nd > 0) {
       std::vector<UpdTask> tz{make_task(M.Z, M.ldz, 1, 0, kwtop, nw, M.zrows, V, nw, nullptr)};

@@ -16,8 +16,12 @@
 //                   window and accumulator U in shared memory
 //   k_apply_u       off-window products U^T X / X U (Sec. 3.2.1), FP64 FFMA
 //   k_extract_eigs  eigenvalues from the standardised diagonal blocks
+#include <cooperative_groups.h>
+
 #include "cta.cuh"
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 __global__ void k_set_int(int* p, int v) {
@@ -96,26 +100,55 @@ __device__ void aed_write_back(double* H, long long ldh, int ktop, int kwtop, in
   }
 }
 
-__global__ void __launch_bounds__(CTA_THREADS) k_aed_small(double* H, long long ldh, int ktop, int kbot, int nw,
-                                                           double* V, int ldv, double* cand_re, double* cand_im,
-                                                           double* vbuf, DeflParams dp, DeflParams dpw, Ctl* ctl) {
+// The AED kernel runs as a cluster of two blocks (Sec. 2.5 step 1 on block
+// 0, the accumulation of its transform V on block 1, see the transform
+// stream in cta.cuh); block 0 then runs steps 2-3 with V in global memory.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CTA_THREADS)
+    k_aed_small(double* H, long long ldh, int ktop, int kbot, int nw, double* V, int ldv, double* cand_re,
+                double* cand_im, double* vbuf, DeflParams dp, DeflParams dpw, Ctl* ctl) {
   extern __shared__ double smem[];
   __shared__ CtaShared sh;
   __shared__ int s_ncand, s_swf;
+  __shared__ VRing ring;
+  cg::cluster_group cluster = cg::this_cluster();
+  const unsigned rank = cluster.block_rank();
   int kwtop = kbot - nw + 1;
   int ldt = nw | 1;
+  if (threadIdx.x == 0) {
+    ring.count = 0;
+    ring.consumed = 0;
+    ring.pushed = 0;
+    ring.err = 0;
+    ring.remote = cluster.map_shared_rank(&ring, rank ^ 1u);
+  }
+  cluster.sync();
+  if (rank == 1) {
+    Mat Vs{smem, ldt};
+    for (int j = 0; j < nw; ++j)
+      for (int i = threadIdx.x; i < nw; i += blockDim.x) Vs(i, j) = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
+    const int timed_out = vring_consume(&ring, Vs, nw);
+    for (int j = 0; j < nw; ++j)
+      for (int i = threadIdx.x; i < nw; i += blockDim.x) V[i + (long long)j * ldv] = Vs(i, j);
+    if (timed_out && threadIdx.x == 0) atomicOr(&ctl->sync_err, 1);
+    cluster.sync();   // V is complete in global memory
+    return;
+  }
   Mat T{smem, ldt};
   Mat Vm{V, ldv};
   for (int j = 0; j < nw; ++j)
-    for (int i = threadIdx.x; i < nw; i += blockDim.x) {
+    for (int i = threadIdx.x; i < nw; i += blockDim.x)
       T(i, j) = (i <= j + 1) ? H[(kwtop + i) + (long long)(kwtop + j) * ldh] : 0.0;
-      Vm(i, j) = (i == j) ? 1.0 : 0.0;
-    }
   double s = (kwtop > ktop) ? H[kwtop + (long long)(kwtop - 1) * ldh] : 0.0;
   __syncthreads();
   long long c0 = clock64();
-  int info = cta_francis(T, nw, 0, nw - 1, Vm, nw, dpw, &sh);
-  if (threadIdx.x == 0) ctl->cyc_schur += clock64() - c0;
+  int info = cta_francis(T, nw, 0, nw - 1, Vm, nw, dpw, &sh, &ring);
+  if (threadIdx.x == 128) vring_push(&ring, 0.0, 0.0, 0.0, 0, 0);   // end of the stream
+  cluster.sync();   // block 1 has applied the stream and written V
+  if (threadIdx.x == 0) {
+    ctl->cyc_schur += clock64() - c0;
+    if (ring.err) atomicOr(&ctl->sync_err, 1);
+  }
   double top;
   int nd = cta_aed_post(T, nw, info, s, Vm, dp, vbuf, cand_re, cand_im, &s_ncand, &top, &s_swf, &sh,
                         &ctl->cyc_defl);
