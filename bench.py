@@ -171,7 +171,7 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def secondary_metrics(api, inputs, torch, np):
+def secondary_metrics(api, inputs, torch, np, peak=None):
     """The other two metrics of the workload list, each next to the plain
     single-matrix path on the same GPU:
       batched:  4096 hess_n matrices, n uniform in [32, 768] (seed 2024), one
@@ -210,6 +210,7 @@ def secondary_metrics(api, inputs, torch, np):
     for s_, h in zip(bufs[0], Hs):
         s_.copy_(h)
     t, info = timed(lambda: api.schur_batched_inplace(*bufs))
+    bst = api.last_stats()
     single = []
     for h in Hs[:16]:
         S1, Z1 = h.clone(), api.new_colmajor(h.shape[0])
@@ -218,8 +219,14 @@ def secondary_metrics(api, inputs, torch, np):
         o = api._lib.make_opts(torch.cuda.current_stream().cuda_stream)
         ts, _ = timed(lambda: api.schur_inplace(S1, Z1, w1, w2, o))
         single.append(ts)
+    bfl = bst["reflector_flops"]
     out["batched"] = {"workload": "4096 hess_n, n uniform in [32,768], seed 2024", "mats_per_s": 4096 / t,
                       "seconds": t, "failed": int(sum(1 for i in info if i)), "launches": 2,
+                      "graph_replayed": bst["graph_built"] == 0,
+                      "algorithmic_flops": bfl, "algorithmic_tflops": bfl / t / 1e12,
+                      "frac_of_peak": (bfl / t / 1e12 / peak) if peak else None,
+                      "flops_note": "counted by the kernel: 4 nr flops per row/column entry of each reflector "
+                                    "of order nr it applies, 2 nw^2 per vector of each AED window product",
                       "single_path_mats_per_s": len(single) / sum(single),
                       "single_path_sample": "first 16 matrices of the batch, one schur_hessenberg call each"}
     del Hs, bufs
@@ -537,7 +544,8 @@ def main():
     del H0
     torch.cuda.empty_cache()
     peaks = fp64_peaks(api, _lib, torch, local)
-    sec = None if args.no_secondary else secondary_metrics(api, inputs, torch, np)
+    sec = None if args.no_secondary else secondary_metrics(api, inputs, torch, np,
+                                                           max(peaks["fma_probe_tflops"], peaks["dgemm_tflops"]))
 
     st = stats[-1]
     # the dominant kernel, k_apply_u (the sweeps' off-window products on H's

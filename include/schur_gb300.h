@@ -114,6 +114,8 @@ typedef struct {
   double aed_cycles_post;
   long long kernel_launches; /* kernels launched by the call (all levels) */
   double t_z_ms;            /* products applied to Z on the Z stream (overlaps the rest) */
+  int graph_built;          /* schur_hessenberg_batched: 1 if this call captured a new graph, 0 if it
+                               replayed the one cached for its batch shape */
 } schur_stats;
 
 /* Fill *opts with the defaults listed above. Returns SCHUR_OK. */
@@ -195,7 +197,14 @@ const char* schur_last_error_detail(void);
 /*
  * schur_hessenberg_batched -- the same reduction for `batch` independent
  * matrices of uneven sizes in ONE persistent kernel launch, replayed from a
- * captured CUDA graph (not in the paper: batching of the method).  Each
+ * captured CUDA graph (not in the paper: batching of the method).  The graph
+ * and its device buffers are cached per batch shape (batch size, the
+ * size table, deflation mode, opts->z_init; up to 4 shapes, least recently
+ * used released): a call with a cached shape uploads its descriptors and
+ * replays the graph.  Calls are serialised by a lock.  schur_last_stats
+ * reports graph_built and, in reflector_flops, the algorithmic flops the
+ * kernel applied (4 nr per row or column entry of each reflector of order
+ * nr, 2 nw^2 per vector of each AED window product).  Each
  * matrix is reduced by one thread block with the same iteration as
  * schur_hessenberg (AED, multishift sweeps, double-shift QR for small
  * blocks, the same deflation conditions), with reflectors applied directly

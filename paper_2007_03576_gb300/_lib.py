@@ -70,6 +70,7 @@ class SchurStats(ctypes.Structure):
         ("aed_cycles_post", c_double),
         ("kernel_launches", ctypes.c_longlong),
         ("t_z_ms", c_double),
+        ("graph_built", c_int),
     ]
 
 

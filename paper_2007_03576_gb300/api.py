@@ -155,13 +155,13 @@ def _ints(xs):
     return (ctypes.c_int * len(xs))(*[int(x) for x in xs])
 
 
-def schur_batched_inplace(Hs, Zs, wrs, wis, z_init=0, deflation="lapack", fixed_thold=0.0):
+def schur_batched_inplace(Hs, Zs, wrs, wis, z_init=0, deflation="lapack", fixed_thold=0.0, nmin=0):
     """One persistent launch over column-major buffers (lists of tensors),
     in place; returns the per-matrix info list."""
     lib = _lib.load()
     b = len(Hs)
     info = (ctypes.c_int * max(b, 1))()
-    o = _lib.make_opts(_stream_ptr().value, z_init=z_init, deflation=deflation, fixed_thold=fixed_thold)
+    o = _lib.make_opts(_stream_ptr().value, z_init=z_init, deflation=deflation, fixed_thold=fixed_thold, nmin=nmin)
     rc = lib.schur_hessenberg_batched(b, _ints([h.shape[0] for h in Hs]), _ptrs(Hs), _ints([_ld(h) for h in Hs]),
                                       _ptrs(Zs), _ints([_ld(z) for z in Zs]), _ptrs(wrs), _ptrs(wis), info,
                                       ctypes.byref(o))

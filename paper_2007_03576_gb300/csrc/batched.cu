@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/schur_gb300.h"
@@ -85,7 +86,7 @@ __device__ void cta_window_product(const Mat& A, int side, int r0, int c0, int n
 // thread, (B) all left products, (C) all right products (and Z).
 // ---------------------------------------------------------------------------
 __device__ void cta_ms_sweep(const Mat& H, int n, int lo, int hi, const double* pairs, int nb, const Mat& Z,
-                             int zrows, BShared* bs) {
+                             int zrows, BShared* bs, double* flops) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int steps = (hi - lo) + 3 * (nb - 1);
   for (int t = 0; t < steps; ++t) {
@@ -123,6 +124,13 @@ __device__ void cta_ms_sweep(const Mat& H, int n, int lo, int hi, const double* 
       }
     }
     __syncthreads();
+    if (tid == 0) {   // algorithmic flops: 4 nr per row / column entry of each reflector
+      double e = 0.0;
+      for (int j = 0; j < nb; ++j)
+        if (bs->nr[j] != 0 && bs->tau[j] != 0.0)
+          e += 4.0 * bs->nr[j] * ((n - bs->k[j]) + (min(bs->k[j] + 3, hi) + 1) + zrows);
+      *flops += e;
+    }
     {  // (B) left products, items spread over all threads
       int base = 0;
       for (int j = 0; j < nb; ++j) {
@@ -195,7 +203,7 @@ __device__ int cta_aed_direct(const Mat& H, int n, const Mat& Z, int ktop, int k
   __syncthreads();
   DeflParams dpw = dp;
   dpw.n = nw;
-  int info = cta_francis(T, nw, 0, nw - 1, V, nw, dpw, sh);
+  int info = cta_francis(T, nw, 0, nw - 1, V, nw, dpw, sh, nullptr, &bs->dval[1]);
   double top;
   int nd = cta_aed_post(T, nw, info, s, V, dp, sc.vbuf, sc.cand_re, sc.cand_im, &bs->ival[1], &top, &bs->ival[2], sh);
   __syncthreads();
@@ -205,6 +213,7 @@ __device__ int cta_aed_direct(const Mat& H, int n, const Mat& Z, int ktop, int k
     if (kwtop > ktop)
       for (int i = tid; i < nw; i += nt) H(kwtop + i, kwtop - 1) = (i == 0) ? top : 0.0;
     __syncthreads();
+    if (tid == 0) bs->dval[1] += 2.0 * nw * nw * ((double)(n - kbot - 1) + kwtop + n);
     if (kbot + 1 < n) cta_window_product(H, 0, kwtop, kbot + 1, n - kbot - 1, nw, sc.V, stage);
     if (kwtop > 0) cta_window_product(H, 1, 0, kwtop, kwtop, nw, sc.V, stage);
     cta_window_product(Z, 1, 0, kwtop, n, nw, sc.V, stage);
@@ -237,7 +246,7 @@ __device__ int cta_schur_one(const Mat& H, int n, const Mat& Z, const BatchedPar
       continue;
     }
     if (m <= P.nmin) {
-      int info = cta_francis(H, n, ktop, kbot, Z, n, dp, sh);
+      int info = cta_francis(H, n, ktop, kbot, Z, n, dp, sh, nullptr, &bs->dval[1]);
       if (info) return info;
       kbot = ktop - 1;
       ndfl = 1;
@@ -260,7 +269,7 @@ __device__ int cta_schur_one(const Mat& H, int n, const Mat& Z, const BatchedPar
     __syncthreads();
     int np = bs->ival[0];
     __syncthreads();
-    if (np > 0) cta_ms_sweep(H, n, ktop, kbot, sc.pairs, np, Z, n, bs);
+    if (np > 0) cta_ms_sweep(H, n, ktop, kbot, sc.pairs, np, Z, n, bs, &bs->dval[1]);
   }
   return (kbot >= 0) ? kbot + 1 : 0;
 }
@@ -275,6 +284,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 3) k_batched(const BatchedDesc* _
   double* smem_T = smem;
   double* stage = smem + (size_t)(P.nw_max | 1) * P.nw_max;
   const BatchedScratch sc = scratch[blockIdx.x];
+  if (threadIdx.x == 0) bs.dval[1] = 0.0;
   // bounded: every iteration consumes one queue entry
   for (int guard = 0; guard <= batch; ++guard) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
@@ -329,6 +339,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 3) k_batched(const BatchedDesc* _
     if (threadIdx.x == 0) info[order[item]] = rc;
     __syncthreads();
   }
+  if (threadIdx.x == 0 && sc.flops) *sc.flops += bs.dval[1];
 }
 
 __global__ void k_batched_prep_z(const BatchedDesc* desc, int batch, int zinit) {
@@ -345,19 +356,19 @@ __global__ void k_batched_prep_z(const BatchedDesc* desc, int batch, int zinit) 
 // ===========================================================================
 namespace schur {
 
-// Default per-bucket table: the autotuner's choice (tune.autotune_batched on
-// GB300, 608 hess_n matrices with n uniform in [32, 768]; timings in the
-// profiles folder).  Windows are capped for the batched engine's shared-memory
-// window.
+// Default per-bucket table and double-shift crossover: the autotuner's choice
+// (tune.autotune_batched and tune.autotune_batched_nmin on GB300, one wave of
+// hess_n matrices per bucket; timings in the profiles folder).  Windows are
+// capped for the batched engine's shared-memory window.
 static void default_batched_params(BatchedParams& P) {
   memset(&P, 0, sizeof(P));
-  P.nmin = 75;
+  P.nmin = 48;
   P.nibble = 14;
   P.exc_period = 6;
   P.nbuckets = 4;
   int mx[4] = {149, 299, 589, 1 << 30};
-  int ns[4] = {4, 8, 32, 16};
-  int nw[4] = {16, 24, 64, 48};
+  int ns[4] = {8, 8, 32, 32};
+  int nw[4] = {24, 24, 64, 64};
   for (int b = 0; b < 4; ++b) {
     P.bucket_max_n[b] = mx[b];
     P.ns[b] = ns[b];
@@ -404,6 +415,95 @@ static size_t batched_smem(const BatchedParams& P) {
   return ((size_t)(P.nw_max | 1) * P.nw_max + (size_t)P.nw_max * B_STAGE_COLS) * sizeof(double);
 }
 
+// One captured graph per batch shape (batch size, grid, parameters, Z
+// initialisation, device): its device buffer holds the descriptors, the
+// largest-first order, the queue counter, the per-matrix status, the
+// per-block scratch and flop counters.  A call uploads the descriptors and
+// the order (the matrices' pointers may change between calls), replays the
+// graph (counter reset, Z = I, the persistent kernel) and reads the status
+// back.  At most BGRAPH_CACHE shapes are kept; the least recently used one
+// is released.
+#define BGRAPH_CACHE 4
+
+struct BGraph {
+  int dev = -1, batch = 0, grid = 0, zinit = 0;
+  BatchedParams P;
+  char* mem = nullptr;
+  size_t off_desc = 0, off_ord = 0, off_cnt = 0, off_info = 0, off_scr = 0, off_flops = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long used = 0;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (mem) cudaFree(mem);
+    exec = nullptr;
+    graph = nullptr;
+    mem = nullptr;
+    batch = 0;
+  }
+};
+
+static std::mutex g_bgraph_mu;
+static BGraph g_bgraph[BGRAPH_CACHE];
+static unsigned long long g_bgraph_clock = 0;
+
+// Builds the graph of one shape into e (device buffers, scratch layout,
+// capture, instantiation).  Throws CudaError.
+static void bgraph_build(BGraph& e, int dev, int batch, int grid, int zinit, const BatchedParams& P, size_t smem,
+                         cudaStream_t st) {
+  e.dev = dev;
+  e.batch = batch;
+  e.grid = grid;
+  e.zinit = zinit;
+  e.P = P;
+  size_t per_block = ((size_t)P.nw_max * P.nw_max + 6 * (size_t)P.nw_max + 2 * (MAX_BULGES_PER_CHAIN + 4)) *
+                     sizeof(double);
+  per_block = (per_block + 255) & ~(size_t)255;
+  e.off_desc = 0;
+  e.off_ord = (e.off_desc + batch * sizeof(BatchedDesc) + 255) & ~(size_t)255;
+  e.off_cnt = (e.off_ord + batch * sizeof(int) + 255) & ~(size_t)255;
+  e.off_info = e.off_cnt + 256;
+  e.off_flops = (e.off_info + batch * sizeof(int) + 255) & ~(size_t)255;
+  e.off_scr = (e.off_flops + grid * sizeof(double) + 255) & ~(size_t)255;
+  const size_t off_sd = (e.off_scr + grid * sizeof(BatchedScratch) + 255) & ~(size_t)255;
+  const size_t total = off_sd + grid * per_block;
+  if (cudaMalloc((void**)&e.mem, total) != cudaSuccess) {
+    cudaGetLastError();
+    e.mem = nullptr;
+    throw CudaError{cudaErrorMemoryAllocation};
+  }
+  std::vector<BatchedScratch> hs(grid);
+  for (int g = 0; g < grid; ++g) {
+    double* base = (double*)(e.mem + off_sd + g * per_block);
+    hs[g].V = base;
+    hs[g].vbuf = base + (size_t)P.nw_max * P.nw_max;
+    hs[g].cand_re = hs[g].vbuf + 4 * P.nw_max;
+    hs[g].cand_im = hs[g].cand_re + P.nw_max;
+    hs[g].pairs = hs[g].cand_im + P.nw_max;
+    hs[g].flops = (double*)(e.mem + e.off_flops) + g;
+  }
+  ck_at(cudaMemcpyAsync(e.mem + e.off_scr, hs.data(), grid * sizeof(BatchedScratch), cudaMemcpyHostToDevice, st),
+        __LINE__);
+  ck_at(cudaStreamSynchronize(st), __LINE__);
+  cudaStream_t cap = nullptr;
+  ck_at(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), __LINE__);
+  cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (err == cudaSuccess) {
+    cudaMemsetAsync(e.mem + e.off_cnt, 0, sizeof(int), cap);
+    cudaMemsetAsync(e.mem + e.off_flops, 0, grid * sizeof(double), cap);
+    k_batched_prep_z<<<std::min(batch, 4 * num_sms()), CTA_THREADS, 0, cap>>>((BatchedDesc*)(e.mem + e.off_desc),
+                                                                              batch, zinit);
+    k_batched<<<grid, CTA_THREADS, smem, cap>>>((BatchedDesc*)(e.mem + e.off_desc), (int*)(e.mem + e.off_ord), batch,
+                                                (int*)(e.mem + e.off_cnt), (int*)(e.mem + e.off_info),
+                                                (BatchedScratch*)(e.mem + e.off_scr), P);
+    err = cudaStreamEndCapture(cap, &e.graph);
+  }
+  cudaStreamDestroy(cap);
+  ck_at(err, __LINE__);
+  ck_at(cudaGraphInstantiate(&e.exec, e.graph, 0), __LINE__);
+}
+
 extern "C" int schur_hessenberg_batched(int batch, const int* n, double* const* H, const int* ldh, double* const* Z,
                                         const int* ldz, double* const* wr, double* const* wi, int* info,
                                         const schur_opts* opts) {
@@ -438,18 +538,39 @@ extern "C" int schur_hessenberg_batched(int batch, const int* n, double* const* 
   if (o.nibble > 0) P.nibble = o.nibble;
   P.mode = o.deflation;
   P.thold = o.fixed_thold;
-  char* mem = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaStream_t cap = nullptr;
   int rc = SCHUR_OK;
+  std::lock_guard<std::mutex> lock(g_bgraph_mu);
   try {
     init_kernel_attributes();
+    int dev = 0;
+    ck_at(cudaGetDevice(&dev), __LINE__);
     size_t smem = batched_smem(P);
     int per_sm = 0;
     ck_at(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, CTA_THREADS, smem), __LINE__);
     int grid = std::min(batch, num_sms() * std::max(1, per_sm));
-    // device memory: descriptors, order, counter, info, per-block scratch
+    const int zinit = o.z_init ? 1 : 0;
+    // the cached graph of this shape, else build one in the least recently used slot
+    BGraph* e = nullptr;
+    for (auto& c : g_bgraph)
+      if (c.exec && c.dev == dev && c.batch == batch && c.grid == grid && c.zinit == zinit &&
+          memcmp(&c.P, &P, sizeof(P)) == 0)
+        e = &c;
+    bool built = false;
+    if (!e) {
+      e = &g_bgraph[0];
+      for (auto& c : g_bgraph)
+        if (!c.exec || c.used < e->used) e = &c;
+      e->release();
+      try {
+        bgraph_build(*e, dev, batch, grid, zinit, P, smem, st);
+      } catch (const CudaError&) {
+        e->release();
+        throw;
+      }
+      built = true;
+    }
+    e->used = ++g_bgraph_clock;
+    // this call's descriptors and largest-first order
     std::vector<BatchedDesc> hd(batch);
     std::vector<int> ord(batch);
     for (int b = 0; b < batch; ++b) {
@@ -457,53 +578,24 @@ extern "C" int schur_hessenberg_batched(int batch, const int* n, double* const* 
       ord[b] = b;
     }
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return n[a] > n[c]; });
-    size_t per_block = ((size_t)P.nw_max * P.nw_max + 6 * (size_t)P.nw_max + 2 * (MAX_BULGES_PER_CHAIN + 4)) *
-                       sizeof(double);
-    per_block = (per_block + 255) & ~(size_t)255;
-    size_t off_desc = 0;
-    size_t off_ord = (off_desc + batch * sizeof(BatchedDesc) + 255) & ~(size_t)255;
-    size_t off_cnt = (off_ord + batch * sizeof(int) + 255) & ~(size_t)255;
-    size_t off_info = off_cnt + 256;
-    size_t off_scr = (off_info + batch * sizeof(int) + 255) & ~(size_t)255;
-    size_t off_sd = (off_scr + grid * sizeof(BatchedScratch) + 255) & ~(size_t)255;
-    size_t total = off_sd + grid * per_block;
-    ck_at(cudaMalloc((void**)&mem, total), __LINE__);
-    std::vector<BatchedScratch> hs(grid);
-    for (int g = 0; g < grid; ++g) {
-      double* base = (double*)(mem + off_sd + g * per_block);
-      hs[g].V = base;
-      hs[g].vbuf = base + (size_t)P.nw_max * P.nw_max;
-      hs[g].cand_re = hs[g].vbuf + 4 * P.nw_max;
-      hs[g].cand_im = hs[g].cand_re + P.nw_max;
-      hs[g].pairs = hs[g].cand_im + P.nw_max;
-    }
-    ck_at(cudaMemcpyAsync(mem + off_desc, hd.data(), batch * sizeof(BatchedDesc), cudaMemcpyHostToDevice, st),
+    ck_at(cudaMemcpyAsync(e->mem + e->off_desc, hd.data(), batch * sizeof(BatchedDesc), cudaMemcpyHostToDevice, st),
           __LINE__);
-    ck_at(cudaMemcpyAsync(mem + off_ord, ord.data(), batch * sizeof(int), cudaMemcpyHostToDevice, st), __LINE__);
-    ck_at(cudaMemcpyAsync(mem + off_scr, hs.data(), grid * sizeof(BatchedScratch), cudaMemcpyHostToDevice, st),
+    ck_at(cudaMemcpyAsync(e->mem + e->off_ord, ord.data(), batch * sizeof(int), cudaMemcpyHostToDevice, st),
           __LINE__);
-    ck_at(cudaStreamSynchronize(st), __LINE__);
-    // one persistent launch, captured into a CUDA graph and replayed
-    ck_at(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), __LINE__);
-    ck_at(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), __LINE__);
-    cudaMemsetAsync(mem + off_cnt, 0, sizeof(int), cap);
-    k_batched_prep_z<<<std::min(batch, 4 * num_sms()), CTA_THREADS, 0, cap>>>((BatchedDesc*)(mem + off_desc), batch,
-                                                                              o.z_init);
-    k_batched<<<grid, CTA_THREADS, smem, cap>>>((BatchedDesc*)(mem + off_desc), (int*)(mem + off_ord), batch,
-                                                (int*)(mem + off_cnt), (int*)(mem + off_info),
-                                                (BatchedScratch*)(mem + off_scr), P);
-    ck_at(cudaStreamEndCapture(cap, &graph), __LINE__);
-    ck_at(cudaGraphInstantiate(&exec, graph, 0), __LINE__);
-    ck_at(cudaGraphLaunch(exec, st), __LINE__);
+    ck_at(cudaGraphLaunch(e->exec, st), __LINE__);
+    memset(&g_stats, 0, sizeof(g_stats));
     g_stats.kernel_launches = 2;
-    ck_at(cudaMemcpyAsync(info, mem + off_info, batch * sizeof(int), cudaMemcpyDeviceToHost, st), __LINE__);
+    g_stats.graph_built = built ? 1 : 0;
+    std::vector<double> fl(grid);
+    ck_at(cudaMemcpyAsync(info, e->mem + e->off_info, batch * sizeof(int), cudaMemcpyDeviceToHost, st), __LINE__);
+    ck_at(cudaMemcpyAsync(fl.data(), e->mem + e->off_flops, grid * sizeof(double), cudaMemcpyDeviceToHost, st),
+          __LINE__);
     ck_at(cudaStreamSynchronize(st), __LINE__);
+    double tot = 0.0;
+    for (double f : fl) tot += f;
+    g_stats.reflector_flops = tot;
   } catch (const CudaError&) {
     rc = SCHUR_ERR_CUDA;
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  if (cap) cudaStreamDestroy(cap);
-  if (mem) cudaFree(mem);
   return rc;
 }

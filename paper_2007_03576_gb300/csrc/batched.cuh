@@ -34,6 +34,7 @@ struct BatchedScratch {   // per thread block, global memory
   double* cand_re;  // nw_max
   double* cand_im;
   double* pairs;    // 2 * (MAX_BULGES_PER_CHAIN + 4)
+  double* flops;    // 1: algorithmic flops this block applied (accumulated over its matrices)
 };
 
 struct BShared;

@@ -530,8 +530,10 @@ __device__ __forceinline__ void exceptional_pair(const Mat& T, int lo, int i, do
 // i+1 when the iteration limit 30*max(10, hi-lo+1) is reached with rows
 // lo..i unreduced.
 // ---------------------------------------------------------------------------
+// flops (optional, thread 0 only): adds the algorithmic flops of the
+// reflectors applied (4 nr per entry of a row or column they touch).
 __device__ inline int cta_francis(const Mat& T, int m, int lo, int hi, const Mat& U, int urows, const DeflParams& dp,
-                                  CtaShared* sh, VRing* ring = nullptr) {
+                                  CtaShared* sh, VRing* ring = nullptr, double* flops = nullptr) {
   int i = hi;
   int itmax = 30 * max(10, hi - lo + 1);
   int total = 0;
@@ -553,6 +555,11 @@ __device__ inline int cta_francis(const Mat& T, int m, int lo, int hi, const Mat
         sprod = a * d - b * c;
       }
       cta_double_shift_sweep(T, m, l, i, ssum, sprod, U, urows, sh, ring);
+      if (flops && cta_tid() == 0) {
+        double e = 0.0;
+        for (int k = l; k < i; ++k) e += 4.0 * min(3, i - k + 1) * ((min(k + 3, i) + 1) + (m - k) + (U.p ? urows : 0));
+        *flops += e;
+      }
     }
     if (l == i) {
       i -= 1;

@@ -107,6 +107,7 @@ extern "C" int schur_hessenberg_noalloc(int n, double* H, int ldh, double* Z, in
   sc.cand_re = sc.vbuf + 4 * NA_NW;
   sc.cand_im = sc.cand_re + NA_NW;
   sc.pairs = sc.cand_im + NA_NW;
+  sc.flops = nullptr;
   const int zero2[4] = {0, 0, 0, 0};
   const int order0 = 0;
   size_t smem = ((size_t)(NA_NW | 1) * NA_NW + (size_t)NA_NW * B_STAGE_COLS) * sizeof(double);

@@ -89,3 +89,27 @@ def test_batched_table_and_zinit():
         api.set_batched_table([], [], [])
     with pytest.raises(RuntimeError):
         api.set_batched_table([10], [1], [16])
+
+
+def test_batched_graph_is_replayed_for_the_same_shape():
+    """The captured graph is cached per batch shape: a second call with the
+    same shape replays it with the new matrices' descriptors (and is just as
+    correct); a different batch size captures a new one.  The kernel's
+    counted algorithmic flops are reported."""
+    sizes = [90, 140, 60]
+    results = []
+    for call, seed in enumerate((41, 42)):
+        Hs = [inputs.hessrand(n, [seed, b]) for b, n in enumerate(sizes)]
+        S, Z, wr, wi, info = api.schur_batched([_dev(h) for h in Hs])
+        st = api.last_stats()
+        results.append(st["graph_built"])
+        assert all(i == 0 for i in info)
+        for h, s_, z_ in zip(Hs, S, Z):
+            _check(h, s_.cpu().numpy(), z_.cpu().numpy())
+        # the work of the iteration on these orders, with Z: of the order of
+        # 10-40 n^3 per matrix
+        work = sum(n ** 3 for n in sizes)
+        assert 2 * work < st["reflector_flops"] < 80 * work, st["reflector_flops"] / work
+    assert results[1] == 0
+    S, Z, wr, wi, info = api.schur_batched([_dev(inputs.hessrand(50, 43))])
+    assert api.last_stats()["graph_built"] == 1 and info == [0]
