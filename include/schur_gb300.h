@@ -87,6 +87,12 @@ typedef struct {
                           LAPACK's NMIN for the small AED task of Sec. 3.2.
                           0 = 160, the largest window one block holds;
                           values above 160 act as 160 */
+  int recompute_shifts;/* 1: when AED leaves at most ns/2 undeflated
+                          candidates, the next sweep's shifts are the
+                          eigenvalues of the trailing min(ns, 160) rows of the
+                          active block (LAPACK's rule, which the paper's
+                          Sec. 5 names as the source of its shift quality
+                          differences); 0 (default): the AED candidates */
 } schur_opts;
 
 /* Statistics of the last schur_hessenberg call on this host thread. */
@@ -116,6 +122,7 @@ typedef struct {
   double t_z_ms;            /* products applied to Z on the Z stream (overlaps the rest) */
   int graph_built;          /* schur_hessenberg_batched: 1 if this call captured a new graph, 0 if it
                                replayed the one cached for its batch shape */
+  int shift_recomputations; /* sweeps whose shifts were recomputed (opts->recompute_shifts) */
 } schur_stats;
 
 /* Fill *opts with the defaults listed above. Returns SCHUR_OK. */

@@ -56,6 +56,7 @@ class Params:
     exc_period: int = 6
     nwin_francis: int = 0    # AED windows up to max(nmin, this) use Francis QR (0: nmin, LAPACK's rule)
     swap_tol: float = 10.0   # a swap is rejected when its residual exceeds swap_tol * u * ||A||_F
+    recompute_shifts: bool = False  # shifts from the trailing ns x ns block when AED leaves <= ns/2
     normH: float = 0.0  # ||H||_F of the input, set by ``schur``
     depth: int = 0      # AED recursion depth (0 = the input matrix)
 
@@ -64,7 +65,7 @@ class Params:
         deflation mode, default shift/window table, one level deeper."""
         return Params(ns=0, nw=0, nmin=self.nmin, nibble=self.nibble, deflation=self.deflation,
                       thold=self.thold, exc_period=self.exc_period, nwin_francis=self.nwin_francis,
-                      swap_tol=self.swap_tol,
+                      swap_tol=self.swap_tol, recompute_shifts=self.recompute_shifts,
                       normH=self.normH, depth=self.depth + 1)
 
 
@@ -568,6 +569,26 @@ def aed(H, Z, ktop, kbot, nw, P, n=None):
     return nd, candidates
 
 
+def recomputed_candidates(H, ktop, kbot, ns, P, n):
+    """Shift recomputation after AED (reading of Sec. 5, the comment on the
+    residuals: LAPACK recomputes the shifts after an AED step under certain
+    conditions, and the same is planned as an option in the paper's
+    library).  The condition and the recomputation follow LAPACK's
+    multishift driver: when AED has left at most ns/2 undeflated
+    candidates, the candidates are replaced by the eigenvalues of the
+    trailing r x r principal submatrix of the active block [ktop, kbot]
+    (r = min(ns, 160, rows of the block); 160 rows is what one thread block
+    of the GPU path holds), computed by double-shift QR on a copy (top to
+    bottom).  Returns None when that QR hits its iteration limit (the AED
+    candidates are kept)."""
+    m = min(ns, 160, kbot - ktop + 1)
+    ks = kbot - m + 1
+    T = np.triu(H[ks:kbot + 1, ks:kbot + 1], -1).copy()
+    if francis_qr(T, np.eye(m), 0, m - 1, P.for_window(), m):
+        return None
+    return block_eigs(T, 0, m)
+
+
 def pairs_from_candidates(cands, npairs):
     """Shift pairs for the next sweep from the AED candidates (reading: the
     paper says the failed candidates become the shifts, Sec. 2.5; take the
@@ -603,6 +624,7 @@ class Stats:
     sweeps: int = 0
     francis: int = 0
     deflated_by_aed: int = 0
+    recomputed: int = 0
 
 
 def qr_block(H, Z, ilo, ihi, P, n=None, stats=None):
@@ -669,6 +691,12 @@ def qr_block(H, Z, ilo, ihi, P, n=None, stats=None):
         if ndfl % P.exc_period == 0:
             pairs = exceptional_pairs(H, ktop, kbot, ns // 2)
         else:
+            if P.recompute_shifts and len(cands) <= ns // 2:
+                rc = recomputed_candidates(H, ktop, kbot, ns, P, n)
+                if rc is not None:
+                    cands = rc
+                    if stats is not None:
+                        stats.recomputed += 1
             pairs = pairs_from_candidates(cands, ns // 2)
             if not pairs:
                 a, b, c, d = H[kbot - 1, kbot - 1], H[kbot - 1, kbot], H[kbot, kbot - 1], H[kbot, kbot]

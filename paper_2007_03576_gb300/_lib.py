@@ -46,6 +46,7 @@ class SchurOpts(ctypes.Structure):
         ("workspace_bytes", c_size_t),
         ("timing", c_int),
         ("nmin_window", c_int),
+        ("recompute_shifts", c_int),
     ]
 
 
@@ -71,6 +72,7 @@ class SchurStats(ctypes.Structure):
         ("kernel_launches", ctypes.c_longlong),
         ("t_z_ms", c_double),
         ("graph_built", c_int),
+        ("shift_recomputations", c_int),
     ]
 
 

@@ -46,6 +46,7 @@ struct Ctl {
   int nswaps;    // swaps performed by the last AED
   long long cyc_schur, cyc_defl, cyc_hess;  // clock64 cycles of the AED sub-steps (accumulated)
   int sync_err;  // the AED kernel's two blocks lost contact (a bounded wait ran out)
+  int recomputed;  // shift recomputations after AED (accumulated)
 };
 
 // One bulge chain in one launch of the chase kernel (Sec. 2.3 / 2.4: a set of

@@ -71,6 +71,9 @@ struct LevelSizes {
   int nsmax;   // most shifts
   size_t arena;  // level 0: doubles of the arena behind the Z stream
   int fmax;      // windows above this order are reduced recursively (need the copy T)
+  // AED candidates, or the eigenvalues of a trailing block of up to
+  // min(nsmax, NW_SMEM_MAX) rows when shifts are recomputed
+  int cand_len() const { return std::max(std::max(nwmax, std::min(nsmax + 8, NW_SMEM_MAX)), 4); }
   size_t bytes() const {
     size_t b = 0;
     b += align_up(sizeof(Ctl));
@@ -78,7 +81,7 @@ struct LevelSizes {
     b += align_up((size_t)nwmax * nwmax * sizeof(double));                       // V
     b += align_up(arena * sizeof(double));
     b += (nwmax > fmax) ? align_up((size_t)nwmax * nwmax * sizeof(double)) : 0;  // T
-    b += 2 * align_up((size_t)std::max(nwmax, 4) * sizeof(double));              // candidates
+    b += 2 * align_up((size_t)cand_len() * sizeof(double));                      // candidates
     b += align_up((size_t)(nsmax + 8) * sizeof(double));                         // pairs
     b += align_up((size_t)4 * std::max(nwmax, 4) * sizeof(double));              // vbuf
     b += align_up((size_t)NW_SMEM_MAX * NW_SMEM_MAX * sizeof(double));           // small-QR U
@@ -156,8 +159,8 @@ void Solver::carve(char* base, int n) {
       arena_cur = 0;
     }
     v.T = (L.nwmax > L.fmax) ? (double*)take((size_t)L.nwmax * L.nwmax * sizeof(double)) : nullptr;
-    v.cand_re = (double*)take((size_t)std::max(L.nwmax, 4) * sizeof(double));
-    v.cand_im = (double*)take((size_t)std::max(L.nwmax, 4) * sizeof(double));
+    v.cand_re = (double*)take((size_t)L.cand_len() * sizeof(double));
+    v.cand_im = (double*)take((size_t)L.cand_len() * sizeof(double));
     v.pairs = (double*)take((size_t)(L.nsmax + 8) * sizeof(double));
     v.vbuf = (double*)take((size_t)4 * std::max(L.nwmax, 4) * sizeof(double));
     v.usmall = (double*)take((size_t)NW_SMEM_MAX * NW_SMEM_MAX * sizeof(double));
@@ -270,6 +273,7 @@ void init_kernel_attributes() {
   allow((const void*)k_smallqr);
   allow((const void*)k_aed_small);
   allow((const void*)k_batched);
+  allow((const void*)k_recompute_shifts);
   ck(apply_u_set_smem(220 * 1024));
   g_attr_done[dev] = true;
 }
@@ -923,6 +927,13 @@ int Solver::aed(const Mat3& M, int lev, int ktop, int kbot, int nw, int ns_max, 
   int saved_phase = cur_update_phase;
   cur_update_phase = PH_AED_UPDATE;
   apply_block_transform(M, kwtop, nw, V, nw, &Lv.ctl->nd, !zasync);
+  if (opts.recompute_shifts) {
+    const int r = std::min(std::min(ns_max, NW_SMEM_MAX), kbot - ktop + 1);
+    ++g_stats.kernel_launches;
+    k_recompute_shifts<<<1, CTA_THREADS, (size_t)(r | 1) * r * sizeof(double), st>>>(
+        M.H, M.ldh, ktop, kbot, ns_max, nw, opts.nibble, opts.nmin, Lv.cand_re, Lv.cand_im, dp, Lv.ctl);
+    ck(cudaGetLastError());
+  }
   ++g_stats.kernel_launches;
   k_make_pairs<<<1, 32, 0, st>>>(M.H, M.ldh, ktop, kbot, std::min(ns_max, Lv.nsmax + 8 - 4), ndfl, 6, Lv.cand_re,
                                  Lv.cand_im, Lv.pairs, Lv.ctl);
@@ -1033,6 +1044,7 @@ extern "C" int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, d
     for (int ph = 0; ph < PH_COUNT; ++ph) s.timer.ms[ph] += s.ztimer.ms[ph] + s.stimer.ms[ph];
     s.write_trace();
     g_stats.aed_cycles_schur = (double)s.hctl->cyc_schur;
+    g_stats.shift_recomputations = s.hctl->recomputed;
     g_stats.aed_cycles_post = (double)s.hctl->cyc_defl;
     g_stats.t_chase_ms = s.timer.ms[PH_CHASE];
     g_stats.t_update_ms = s.timer.ms[PH_UPDATE];

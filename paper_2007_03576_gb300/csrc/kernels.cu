@@ -196,6 +196,62 @@ __global__ void __launch_bounds__(CTA_THREADS) k_aed_big_post(double* H, long lo
 }
 
 // ---------------------------------------------------------------------------
+// Shift recomputation after AED (opts.recompute_shifts; LAPACK's rule): when
+// a sweep follows and AED left at most ns/2 undeflated candidates, the
+// candidates become the eigenvalues of the trailing r x r principal
+// submatrix of the active block (r = min(ns, NW_SMEM_MAX, rows)), computed by
+// double-shift QR on a copy in shared memory; on a QR failure the AED
+// candidates are kept.  kbot_old: the block's last row before AED.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(CTA_THREADS) k_recompute_shifts(const double* H, long long ldh, int ktop,
+                                                                  int kbot_old, int ns_max, int nw, int nibble,
+                                                                  int nmin, double* cand_re, double* cand_im,
+                                                                  DeflParams dp, Ctl* ctl) {
+  extern __shared__ double smem[];
+  __shared__ CtaShared sh;
+  const int nd = ctl->nd;
+  const int kbot = kbot_old - nd;
+  const int mblk = kbot - ktop + 1;
+  // the same decisions as the driver: no sweep follows in these cases
+  if (mblk <= nmin) return;
+  if (nd > 0 && 100 * nd > nibble * nw) return;
+  int ns = min(ns_max, mblk - 1);
+  ns -= ns % 2;
+  if (ctl->ncand > ns / 2) return;
+  const int m = min(min(ns, NW_SMEM_MAX), mblk);
+  if (m < 2) return;
+  const int ks = kbot - m + 1;
+  const int ldt = m | 1;
+  Mat T{smem, ldt};
+  for (int j = 0; j < m; ++j)
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+      T(i, j) = (i <= j + 1) ? H[(ks + i) + (long long)(ks + j) * ldh] : 0.0;
+  __syncthreads();
+  DeflParams dpw = dp;
+  dpw.n = m;
+  const int info = cta_francis(T, m, 0, m - 1, Mat{nullptr, 1}, 0, dpw, &sh);
+  __syncthreads();
+  if (info != 0 || threadIdx.x != 0) return;
+  int c = 0, j = 0;
+  while (j < m) {
+    if (j + 1 < m && T(j + 1, j) != 0.0) {
+      double r1, i1, r2, i2;
+      eig2x2(T(j, j), T(j, j + 1), T(j + 1, j), T(j + 1, j + 1), r1, i1, r2, i2);
+      cand_re[c] = r1; cand_im[c] = i1; ++c;
+      cand_re[c] = r2; cand_im[c] = i2; ++c;
+      j += 2;
+    } else {
+      cand_re[c] = T(j, j);
+      cand_im[c] = 0.0;
+      ++c;
+      j += 1;
+    }
+  }
+  ctl->ncand = c;
+  ctl->recomputed += 1;
+}
+
+// ---------------------------------------------------------------------------
 // Shift pairs for the next sweep (one thread).  Reading of Sec. 2.5: the
 // undeflated AED candidates become the shifts -- the bottom-most ones, complex
 // conjugates kept together, real shifts paired in order of appearance; an

@@ -14,6 +14,8 @@ __global__ void k_copy_window(const double* H, long long ldh, int kwtop, int nw,
 __global__ void k_aed_big_post(double* H, long long ldh, int ktop, int kbot, int nw, double* T, int ldt, double* V,
                                int ldv, double* cand_re, double* cand_im, double* vbuf, DeflParams dp, Ctl* ctl,
                                int inner_info);
+__global__ void k_recompute_shifts(const double* H, long long ldh, int ktop, int kbot_old, int ns_max, int nw,
+                                   int nibble, int nmin, double* cand_re, double* cand_im, DeflParams dp, Ctl* ctl);
 __global__ void k_make_pairs(const double* H, long long ldh, int ktop, int kbot_old, int ns_max, int ndfl_host,
                              int exc_period, const double* cand_re, const double* cand_im, double* pairs, Ctl* ctl);
 __global__ void k_chase(double* H, long long ldh, const double* pairs, double* Ubuf,

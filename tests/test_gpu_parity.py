@@ -331,3 +331,22 @@ def test_fastmath_against_ieee():
     pos = x > 0
     ulp_rs = np.abs(r[pos, 2] - r[pos, 3]) / np.spacing(np.abs(r[pos, 3]))
     assert np.max(ulp_rs) <= 2.0, np.max(ulp_rs)
+
+
+@pytest.mark.parametrize("mode", ["lapack", "norm"])
+def test_recompute_shifts_vs_oracle(mode):
+    """Shift recomputation after AED (opts.recompute_shifts; LAPACK's rule):
+    with windows of at most ns / 2 rows every sweep takes the eigenvalues of
+    the trailing ns x ns block as shifts, on the GPU and in the oracle; both
+    reductions are valid and agree on the spectrum."""
+    n = 300
+    H = inputs.hessrand(n, 777)
+    S, Z, wr, wi, info = api.schur(_dev(H), n_shifts=16, aed_window=8, nmin=24, deflation=mode, recompute_shifts=True)
+    assert info == 0
+    assert api.last_stats()["shift_recomputations"] > 0
+    _check_result(H, _np(S), _np(Z))
+    st = qr.Stats()
+    So, Zo, wro, wio, _ = qr.schur(H, params=qr.Params(ns=16, nw=8, nmin=24, deflation=mode, recompute_shifts=True),
+                                   stats=st)
+    assert st.recomputed > 0
+    _eig_match(_np(wr) + 1j * _np(wi), wro + 1j * wio, So, np.linalg.norm(H))

@@ -641,3 +641,34 @@ def test_aed_halts_reordering_on_rejected_swap():
     # the bottom-up test deflates the same leading run of blocks until the
     # first failed candidate has to move; both runs agree on that run
     assert nd_r >= 0
+
+
+# ------------------------------------------------ shift recomputation
+
+
+def test_recomputed_candidates_are_the_trailing_block_eigenvalues():
+    """Shift recomputation after AED (LAPACK's rule, named by the paper in
+    Sec. 5): the candidates become the eigenvalues of the trailing r x r
+    principal submatrix of the active block (checked against LAPACK on the
+    same block)."""
+    H = inputs.hessrand(90, 512)
+    P = qr.Params()
+    c = qr.recomputed_candidates(H, 10, 89, 16, P, 90)
+    assert len(c) == 16
+    ref = scipy.linalg.eigvals(H[74:90, 74:90])
+    _eig_close(np.array([complex(*z) for z in c]), ref, 1e-11 * np.linalg.norm(H[74:90, 74:90]))
+
+
+def test_recompute_shifts_run_is_a_valid_schur_form():
+    """With small windows (AED can return at most nw <= ns / 2 candidates)
+    every sweep recomputes its shifts; the reduction stays a valid Schur
+    factorisation with LAPACK's eigenvalues."""
+    n = 160
+    H = inputs.hessrand(n, 513)
+    st = qr.Stats()
+    S, Z, wr, wi, info = qr.schur(H, params=qr.Params(ns=16, nw=8, nmin=24, recompute_shifts=True), stats=st)
+    # every sweep recomputes, except those that take exceptional shifts (at
+    # most every 6th iteration without a deflation)
+    assert info == 0 and st.sweeps - st.sweeps // 6 <= st.recomputed <= st.sweeps
+    _check_schur(H, S, Z)
+    _eig_close(wr + 1j * wi, scipy.linalg.eigvals(H), 1e-9 * np.linalg.norm(H))
