@@ -262,7 +262,7 @@ def secondary_metrics(api, inputs, torch, np, peak=None):
 # divided by the flops those launches execute), valid for the kernel source
 # whose hash is recorded; scaled to an average launch of the benchmark by its
 # executed flops.
-APPLY_U_CAPTURE = {"sha": "bb05e315c431c5f3", "dram_bytes_per_exec_flop": 7.862e6 / (2184192 * 64),
+APPLY_U_CAPTURE = {"sha": "9fd69261561f1af4", "dram_bytes_per_exec_flop": 7.8669e6 / (1739896 * 64),
                    "case": "n=5000 hess_n, 64 shifts, window 128; 3 launches of k_apply_u<64> after 300"}
 
 
