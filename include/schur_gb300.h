@@ -123,6 +123,8 @@ typedef struct {
   int graph_built;          /* schur_hessenberg_batched: 1 if this call captured a new graph, 0 if it
                                replayed the one cached for its batch shape */
   int shift_recomputations; /* sweeps whose shifts were recomputed (opts->recompute_shifts) */
+  double flops;             /* schur_hessenberg_reduce, schur_eigenvectors: algorithmic FP64 flops of
+                               the call (LAPACK's operation counts for the same work) */
 } schur_stats;
 
 /* Fill *opts with the defaults listed above. Returns SCHUR_OK. */
@@ -275,6 +277,60 @@ int schur_eig_backward_batched(int batch, const int* n, double* const* S, const 
                                const int* ldz, double* const* wr, double* const* wi, double* const* gwr,
                                double* const* gwi, double* const* dH, const int* lddh,
                                const schur_opts* opts);
+
+/* ---------------------------------------------------------------------
+ * The phases around the QR iteration (Sec. 1): reduction of a general
+ * matrix to Hessenberg form before it (phase i) and eigenvectors from the
+ * Schur form after it (phase iii).  Together with schur_hessenberg they give
+ * the eigen-decomposition of a general matrix on the device:
+ *   schur_hessenberg_reduce(A -> H, Q);  schur_hessenberg(H -> S, Z = Q Z_QR,
+ *   opts.z_init = 1);  schur_eigenvectors(S, Z -> X).
+ * Same conventions as above: device pointers owned by the caller,
+ * column-major, synchronous on opts->stream, no exceptions.
+ * --------------------------------------------------------------------- */
+
+/*
+ * schur_hessenberg_reduce -- Householder reduction A = Q H Q^T of a general
+ * n x n matrix (phase (i), Sec. 1; the textbook unblocked reduction with
+ * LAPACK dgehrd's reflector convention beta = -sign(alpha) ||x||, so H equals
+ * dgehrd's up to rounding).
+ *   A   in: the matrix; out: H, with the entries below the first
+ *       subdiagonal set to 0.                                      (args 2-3)
+ *   Q   out: the orthogonal factor (n x n), or NULL to skip it.    (args 4-5)
+ * Scratch: schur_hessenberg_reduce_workspace(n) bytes, from
+ * opts->workspace when it is set (SCHUR_ERR_WORKSPACE if smaller), else
+ * allocated and freed by the call.  Returns SCHUR_ERR_NONFINITE (A is left
+ * unchanged) if A holds a NaN or Inf.  Sets schur_stats.flops
+ * ((10/3) n^3 for H, (4/3) n^3 more for Q) and kernel_launches.
+ */
+int schur_hessenberg_reduce(int n, double* A, int lda, double* Q, int ldq, const schur_opts* opts);
+int schur_hessenberg_reduce_workspace(int n, size_t* bytes);
+
+/*
+ * schur_eigenvectors -- right eigenvectors of H = Z S Z^T from its real
+ * Schur form (phase (iii), Sec. 1).
+ *   S      the standardised quasi-triangular factor (schur_hessenberg's output
+ *          H); only its upper quasi-triangular part is read.      (args 2-3)
+ *   Z      the Schur vectors (n x n); NULL: X receives the eigenvectors of S
+ *          itself.                                                  (args 4-5)
+ *   wr, wi the eigenvalues schur_hessenberg returned for this S (device,
+ *          length n; a pair has wi > 0 first).                      (args 6-7)
+ *   X      out (n x n): column i = the eigenvector of a real lambda_i; for a
+ *          pair (i, i+1), columns i and i+1 = real and imaginary parts of
+ *          the eigenvector of wr[i] + i wi[i] (its conjugate belongs to
+ *          lambda_{i+1}).  Every (complex) vector has unit 2-norm; the phase
+ *          is that of the back substitution started from 1 (1x1 block) or
+ *          from (b, lambda - a) on a 2x2 block [[a, b], [c, d]].    (args 8-9)
+ * A pivot of magnitude below smin = max(2^-52 ||S||_F, 1e-300) is replaced by
+ * smin (nearly repeated eigenvalues).  The vectors are not protected against
+ * overflow beyond that (growth past ~1e300 needs a departure from normality
+ * of that order).  Scratch: schur_eigenvectors_workspace(n, Z != NULL)
+ * bytes (an n x n buffer when Z is given), from opts->workspace when set,
+ * else allocated by the call.  Sets schur_stats.flops (n^3/3 + n^3 with Z).
+ */
+int schur_eigenvectors(int n, const double* S, int lds, const double* Z, int ldz, const double* wr,
+                       const double* wi, double* X, int ldx, const schur_opts* opts);
+int schur_eigenvectors_workspace(int n, int with_z, size_t* bytes);
 
 /* ---------------------------------------------------------------------
  * Single steps of the method, exported so that each can be checked on its

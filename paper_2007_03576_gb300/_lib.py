@@ -73,6 +73,7 @@ class SchurStats(ctypes.Structure):
         ("t_z_ms", c_double),
         ("graph_built", c_int),
         ("shift_recomputations", c_int),
+        ("flops", c_double),
     ]
 
 
@@ -102,6 +103,11 @@ _SIGS = {
     "schur_hessenberg_noalloc": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p,
                                          P(SchurOpts)]),
     "schur_fp64_fma_probe": (c_int, [c_int, c_int, c_void_p, P(c_double), P(SchurOpts)]),
+    "schur_hessenberg_reduce": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, P(SchurOpts)]),
+    "schur_hessenberg_reduce_workspace": (c_int, [c_int, P(c_size_t)]),
+    "schur_eigenvectors": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int,
+                                   P(SchurOpts)]),
+    "schur_eigenvectors_workspace": (c_int, [c_int, c_int, P(c_size_t)]),
     "schur_chase_schedule": (c_int, [c_int, c_int, c_int, c_int, c_int, c_void_p, P(c_int), P(c_int), P(c_int)]),
     "schur_vigilant_eval": (c_int, [c_int, c_void_p, c_int, c_double, c_double, c_int, c_void_p, P(SchurOpts)]),
     "schur_spike_eval": (c_int, [c_int, c_void_p, c_int, c_double, c_double, c_int, c_void_p, P(SchurOpts)]),

@@ -249,3 +249,74 @@ class Eigvals(torch.autograd.Function):
 
 def eigvals(H):
     return Eigvals.apply(H)
+
+
+def hessenberg_reduce(A, want_q=True, workspace=None):
+    """Householder reduction A = Q H Q^T of a general square matrix (the
+    phase before the QR iteration, Sec. 1); returns (H, Q), Q None when
+    want_q is False.  A itself is not modified."""
+    lib = _lib.load()
+    n = A.shape[0]
+    H = colmajor(A.detach())
+    if H.data_ptr() == A.data_ptr():
+        H = H.clone()
+    Q = new_colmajor(n, device=A.device) if want_q else None
+    o = _lib.make_opts(_stream_ptr().value)
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    rc = lib.schur_hessenberg_reduce(n, H.data_ptr(), _ld(H), Q.data_ptr() if Q is not None else None,
+                                     _ld(Q) if Q is not None else 1, ctypes.byref(o))
+    _check(rc, "schur_hessenberg_reduce")
+    return H, Q
+
+
+def eigenvectors(S, Z, wr, wi, workspace=None):
+    """Right eigenvectors of H = Z S Z^T from its real Schur form (S, Z, wr,
+    wi as returned by ``schur``); Z None gives those of S.  Returns X in
+    LAPACK's real format (a complex pair (i, i+1) stores the real and
+    imaginary parts of the eigenvector of wr[i] + i wi[i] in columns i and
+    i + 1); every vector has unit 2-norm."""
+    lib = _lib.load()
+    n = S.shape[0]
+    Sc = colmajor(S.detach())
+    Zc = colmajor(Z.detach()) if Z is not None else None
+    X = new_colmajor(n, device=S.device)
+    o = _lib.make_opts(_stream_ptr().value)
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    rc = lib.schur_eigenvectors(n, Sc.data_ptr(), _ld(Sc), Zc.data_ptr() if Zc is not None else None,
+                                _ld(Zc) if Zc is not None else 1, wr.contiguous().data_ptr(),
+                                wi.contiguous().data_ptr(), X.data_ptr(), _ld(X), ctypes.byref(o))
+    _check(rc, "schur_eigenvectors")
+    return X
+
+
+def complex_eigenvectors(X, wi):
+    """Complex n x n eigenvector matrix from LAPACK's real format (layout
+    conversion only)."""
+    n = X.shape[0]
+    Xc = X.to(torch.complex128)
+    w = wi.detach().cpu().tolist()
+    i = 0
+    while i < n:
+        if w[i] > 0.0 and i + 1 < n:
+            re, im = X[:, i].clone(), X[:, i + 1].clone()
+            Xc[:, i] = torch.complex(re, im)
+            Xc[:, i + 1] = torch.complex(re, -im)
+            i += 2
+        else:
+            i += 1
+    return Xc
+
+
+def eig(A, **schur_kw):
+    """Eigenvalues and right eigenvectors of a general square matrix, every
+    phase on the device: Householder reduction, multishift QR with AED
+    (accumulating the reduction's Q), eigenvectors from the Schur form.
+    Returns (wr, wi, X, info) with X in LAPACK's real format."""
+    H, Q = hessenberg_reduce(A)
+    S, Z, wr, wi, info = schur(H, Q, **schur_kw)
+    X = eigenvectors(S, Z, wr, wi)
+    return wr, wi, X, info

@@ -53,6 +53,10 @@ SCALAR_CASES = [
      {0: [-1], 1: [None], 2: [-1, 3], 5: [0], 6: [None]}),
     ("schur_spike_eval", [N, DEV, 0, 0.0, 1.0, 4, DEV],
      {0: [-1], 1: [None], 2: [-1, 3], 5: [0], 6: [None]}),
+    ("schur_hessenberg_reduce", [N, DEV, N, DEV, N],
+     {0: [-1], 1: [None], 2: [N - 1, 0], 4: [N - 1]}),
+    ("schur_eigenvectors", [N, DEV, N, DEV, N, DEV, DEV, DEV, N],
+     {0: [-1], 1: [None], 2: [N - 1], 4: [N - 1], 5: [None], 6: [None], 7: [None], 8: [N - 1]}),
 ]
 
 
@@ -141,3 +145,22 @@ def test_noalloc_order_limit_and_workspace_args():
     assert lib.schur_workspace_size(N, None, ctypes.byref(b)) == 0 and b.value > 0
     assert lib.schur_default_opts(None) == -1
     assert lib.schur_last_stats(None) == -1
+
+
+def test_phase_workspace_sizes():
+    """Scratch sizes of the reduction and eigenvector entry points (host
+    arithmetic only): the eigenvector scratch holds an n x n buffer when Z is
+    given; bad arguments return their index."""
+    lib = _lib.load()
+    b = ctypes.c_size_t(0)
+    assert lib.schur_hessenberg_reduce_workspace(1000, ctypes.byref(b)) == 0
+    assert 2 * 1000 * 8 <= b.value < 64 * 1024
+    assert lib.schur_hessenberg_reduce_workspace(-1, ctypes.byref(b)) == -1
+    assert lib.schur_hessenberg_reduce_workspace(10, None) == -2
+    assert lib.schur_eigenvectors_workspace(1000, 1, ctypes.byref(b)) == 0
+    with_z = b.value
+    assert with_z >= 1000 * 1000 * 8
+    assert lib.schur_eigenvectors_workspace(1000, 0, ctypes.byref(b)) == 0
+    assert b.value < with_z - 1000 * 1000 * 8 + 4096
+    assert lib.schur_eigenvectors_workspace(-1, 0, ctypes.byref(b)) == -1
+    assert lib.schur_eigenvectors_workspace(10, 0, None) == -3
