@@ -254,6 +254,29 @@ def secondary_metrics(api, inputs, torch, np, peak=None):
                        "failed": int(sum(1 for i in info if i)),
                        "single_path_backward_over_forward": one_b / one_f,
                        "single_path_sample": "first 8 matrices, schur_hessenberg + schur_eig_backward each"}
+    del Hs, bufs
+    torch.cuda.empty_cache()
+    # the phases around the iteration at n = 4096: Householder reduction of a
+    # dense N(0,1) matrix (H and Q), eigenvectors of a hess_n Schur form
+    n = 4096
+    A = inputs.gaussian(n, 2022)
+    Ad = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+    api.hessenberg_reduce(Ad)                           # warm-up
+    tr, _ = timed(lambda: api.hessenberg_reduce(Ad))
+    rfl = api.last_stats()["flops"]
+    H = inputs.hessrand(n, 2021)
+    S, Z, wr1, wi1, _ = api.schur(torch.from_numpy(np.ascontiguousarray(H.T)).cuda().t())
+    api.eigenvectors(S, Z, wr1, wi1)                    # warm-up
+    te, _ = timed(lambda: api.eigenvectors(S, Z, wr1, wi1))
+    efl = api.last_stats()["flops"]
+    out["phases_n4096"] = {
+        "reduction": {"workload": "dense N(0,1) n=4096 seed 2022 -> H, Q", "seconds": tr,
+                      "algorithmic_flops": rfl, "tflops": rfl / tr / 1e12,
+                      "frac_of_peak": (rfl / tr / 1e12 / peak) if peak else None},
+        "eigenvectors": {"workload": "hess_n n=4096 seed 2021 Schur form -> X = Z X_S", "seconds": te,
+                         "algorithmic_flops": efl, "tflops": efl / te / 1e12,
+                         "frac_of_peak": (efl / te / 1e12 / peak) if peak else None},
+        "flops_note": "reduction (10/3 + 4/3) n^3, eigenvectors n^3/3 + n^3 (the counts of the same work in LAPACK)"}
     return out
 
 

@@ -33,8 +33,8 @@
 //               written over x;
 //   k_hr_left   A[j+1:, c] <- P_j A[j+1:, c] for c >= j+1, one warp per
 //               column (dot pass, then update pass re-reading from L1/L2);
-//   k_hr_right  A[:, j+1:] <- A[:, j+1:] P_j on 16-row slabs (half-warps on
-//               consecutive rows of one column: 128-byte segments); each slab
+//   k_hr_right  A[:, j+1:] <- A[:, j+1:] P_j on 8-row slabs (quarter-warps on
+//               consecutive rows of one column: 64-byte segments); each slab
 //               also writes its part of the sum of squares of the new column
 //               j+1 below row j+2, the norm of step j+1's reflector.
 // Q formation reuses k_hr_left with the stored tau_j and v_j.
@@ -51,7 +51,7 @@ namespace {
 
 constexpr int HR_THREADS = 256;       // 8 warps
 constexpr int HR_WARPS = HR_THREADS / 32;
-constexpr int HR_SLAB = 16;           // rows per block of k_hr_right
+constexpr int HR_SLAB = 8;            // rows per block of k_hr_right
 constexpr int HR_GROUPS = HR_THREADS / HR_SLAB;   // column groups per slab
 
 // Deterministic block sum: strided per-thread sums, a fixed shuffle tree,
@@ -154,34 +154,52 @@ __global__ void __launch_bounds__(HR_THREADS) k_hr_left(double* __restrict__ M, 
     const double w = tau * (mc[j + 1] + d);
     __syncwarp();
     if (lane == 0) mc[j + 1] -= w;
-    for (p = j + 2 + lane; p < n; p += 32) mc[p] = fma(-w, v[p], mc[p]);
+    for (p = j + 2 + lane; p + 96 < n; p += 128) {
+      const double e0 = mc[p], e1 = mc[p + 32], e2 = mc[p + 64], e3 = mc[p + 96];
+      const double v0 = v[p], v1 = v[p + 32], v2 = v[p + 64], v3 = v[p + 96];
+      mc[p] = fma(-w, v0, e0);
+      mc[p + 32] = fma(-w, v1, e1);
+      mc[p + 64] = fma(-w, v2, e2);
+      mc[p + 96] = fma(-w, v3, e3);
+    }
+    for (; p < n; p += 32) mc[p] = fma(-w, v[p], mc[p]);
   }
 }
 
-// A[:, j+1:n] <- A[:, j+1:n] P_j for the 16 rows of this block; writes the
-// block's part of sum_{r >= j+3} A[r, j+1]^2 (after the update) to part[].
+// A[:, j+1:n] <- A[:, j+1:n] P_j for the HR_SLAB rows of this block; writes
+// the block's part of sum_{r >= j+3} A[r, j+1]^2 (after the update) to
+// part[].  Each thread walks its row through every HR_GROUPS-th column, four
+// columns per iteration with their loads issued together (the kernel is
+// limited by load latency, not by the FP64 pipe, when fewer loads are in
+// flight).
 __global__ void __launch_bounds__(HR_THREADS) k_hr_right(double* __restrict__ A, long long lda, int n, int j,
                                                          const double* __restrict__ refl, double* __restrict__ part) {
   __shared__ double red[HR_GROUPS][HR_SLAB + 1];
   __shared__ double gsh[HR_SLAB];
   const double tau = refl[2 * j];
   const double* x = A + (long long)j * lda;   // v of step j below row j+1
-  const int rl = threadIdx.x & (HR_SLAB - 1);
+  const int rl = threadIdx.x % HR_SLAB;
   const int g = threadIdx.x / HR_SLAB;
   const int row = blockIdx.x * HR_SLAB + rl;
   const bool rok = row < n;
   double* Ar = A + row;
+  const long long step = (long long)HR_GROUPS * lda;
   if (tau != 0.0) {
-    double a0 = 0.0, a1 = 0.0;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     if (rok) {
       int c = j + 2 + g;
-      for (; c + HR_GROUPS < n; c += 2 * HR_GROUPS) {
-        a0 = fma(Ar[(long long)c * lda], x[c], a0);
-        a1 = fma(Ar[(long long)(c + HR_GROUPS) * lda], x[c + HR_GROUPS], a1);
+      const double* e = Ar + (long long)c * lda;
+      for (; c + 3 * HR_GROUPS < n; c += 4 * HR_GROUPS, e += 4 * step) {
+        const double e0 = e[0], e1 = e[step], e2 = e[2 * step], e3 = e[3 * step];
+        const double v0 = x[c], v1 = x[c + HR_GROUPS], v2 = x[c + 2 * HR_GROUPS], v3 = x[c + 3 * HR_GROUPS];
+        a0 = fma(e0, v0, a0);
+        a1 = fma(e1, v1, a1);
+        a2 = fma(e2, v2, a2);
+        a3 = fma(e3, v3, a3);
       }
-      if (c < n) a0 = fma(Ar[(long long)c * lda], x[c], a0);
+      for (; c < n; c += HR_GROUPS, e += step) a0 = fma(e[0], x[c], a0);
     }
-    red[g][rl] = a0 + a1;
+    red[g][rl] = (a0 + a1) + (a2 + a3);
   }
   __syncthreads();
   if (threadIdx.x < HR_SLAB) {
@@ -198,16 +216,23 @@ __global__ void __launch_bounds__(HR_THREADS) k_hr_right(double* __restrict__ A,
     }
     gsh[rl] = gv;
     double sq = (rok && row >= j + 3) ? a1 * a1 : 0.0;
-    for (int o = HR_SLAB / 2; o > 0; o >>= 1) sq += __shfl_xor_sync(0x0000ffffu, sq, o);
+    for (int o = HR_SLAB / 2; o > 0; o >>= 1) sq += __shfl_xor_sync((1u << HR_SLAB) - 1u, sq, o);
     if (threadIdx.x == 0) part[blockIdx.x] = sq;
   }
   __syncthreads();
   if (tau != 0.0 && rok) {
     const double gv = gsh[rl];
-    for (int c = j + 2 + g; c < n; c += HR_GROUPS) {
-      double* e = Ar + (long long)c * lda;
-      *e = fma(-gv, x[c], *e);
+    int c = j + 2 + g;
+    double* e = Ar + (long long)c * lda;
+    for (; c + 3 * HR_GROUPS < n; c += 4 * HR_GROUPS, e += 4 * step) {
+      const double e0 = e[0], e1 = e[step], e2 = e[2 * step], e3 = e[3 * step];
+      const double v0 = x[c], v1 = x[c + HR_GROUPS], v2 = x[c + 2 * HR_GROUPS], v3 = x[c + 3 * HR_GROUPS];
+      e[0] = fma(-gv, v0, e0);
+      e[step] = fma(-gv, v1, e1);
+      e[2 * step] = fma(-gv, v2, e2);
+      e[3 * step] = fma(-gv, v3, e3);
     }
+    for (; c < n; c += HR_GROUPS, e += step) e[0] = fma(-gv, x[c], e[0]);
   }
 }
 
