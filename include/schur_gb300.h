@@ -333,9 +333,63 @@ int schur_eigenvectors(int n, const double* S, int lds, const double* Z, int ldz
 int schur_eigenvectors_workspace(int n, int with_z, size_t* bytes);
 
 /* ---------------------------------------------------------------------
+ * The generalized case (the paper's remarks in Sec. 1, 2.1, 2.2 and 3.4):
+ * the generalized real Schur form (S, T) = Q^T (H, T0) Z of a
+ * Hessenberg-triangular pair, by the double-shift QZ iteration.
+ * --------------------------------------------------------------------- */
+
+/*
+ * schur_qz -- (H, T) upper Hessenberg / upper triangular (n x n, device)
+ * are overwritten by S (quasi upper triangular) and T (upper triangular):
+ *   - a 2x2 diagonal block of S holds a complex conjugate pair, and T's block
+ *     there is diagonal with positive entries (LAPACK's standardised form);
+ *     a pair with real eigenvalues is split;
+ *   - |T_ii| <= 2^-52 ||T||_F is an infinite eigenvalue: T_ii is set to 0 and
+ *     the zero is chased up to the top of its unreduced block and split off
+ *     there (Sec. 2.1 / 3.4);
+ *   - entries of H below the subdiagonal and of T below the diagonal are
+ *     ignored on entry and zero on exit.
+ *   Q, Z (args 6-9): when opts->want_z (default 1), the transformations are
+ *     accumulated: z_init = 0 sets Q = Z = I first, z_init = 1 multiplies the
+ *     given Q1, Z1 (e.g. from a Hessenberg-triangular reduction) in place.
+ *   alphar, alphai, beta (device, length n; args 10-12): eigenvalue i is
+ *     (alphar_i + i alphai_i) / beta_i; beta_i = 0 for an infinite one; a
+ *     complex pair has alphai > 0 first.
+ * Method: one thread block runs the whole double-shift iteration on the pair
+ * (bulge of (H T^-1 - l1)(H T^-1 - l2) e1, left 3x3 reflectors, right
+ * reflectors restoring T, Sec. 2.2 remark), exceptional shifts every 10th
+ * iteration without deflation; no multishift sweeps or AED for pairs.
+ * Returns SCHUR_OK, 1 + the top row of a block that did not converge within
+ * 30 x (its order) iterations, SCHUR_ERR_NONFINITE (pair unchanged) or
+ * another negative error.  Sets schur_stats.kernel_launches.
+ */
+int schur_qz(int n, double* H, int ldh, double* T, int ldt, double* Q, int ldq, double* Z, int ldz,
+             double* alphar, double* alphai, double* beta, const schur_opts* opts);
+
+/* schur_qz for `batch` pairs in one launch, one thread block per pair; the
+ * arrays are host arrays of device pointers / ints as in
+ * schur_hessenberg_batched; info (host, length batch) receives each pair's
+ * schur_qz status.  Returns SCHUR_OK or a negative error (a bad argument i
+ * returns -i, also when only one pair's entry is bad). */
+int schur_qz_batched(int batch, const int* n, double* const* H, const int* ldh, double* const* T, const int* ldt,
+                     double* const* Q, const int* ldq, double* const* Z, const int* ldz, double* const* alphar,
+                     double* const* alphai, double* const* beta, int* info, const schur_opts* opts);
+
+/* ---------------------------------------------------------------------
  * Single steps of the method, exported so that each can be checked on its
  * own against the CPU oracle.  Same conventions as above.
  * --------------------------------------------------------------------- */
+
+/*
+ * schur_qz_sweep -- one double-shift QZ sweep (Sec. 2.2 remark) on the
+ * unreduced block lo..hi (0-based, hi - lo >= 2) of the Hessenberg-triangular
+ * pair (H, T) with the shift pair given as ssum = l1 + l2, sprod = l1 l2,
+ * full generalized Schur form mode (rows 0.. and columns ..n-1 updated);
+ * Q and Z (both or neither) accumulate the transformations.  T's diagonal
+ * entries lo, lo+1 and hi-2..hi must be nonzero.
+ */
+int schur_qz_sweep(int n, double* H, int ldh, double* T, int ldt, double* Q, int ldq, double* Z, int ldz, int lo,
+                   int hi, double ssum, double sprod, const schur_opts* opts);
 
 /*
  * schur_sweep -- one tightly-coupled multishift sweep (Sec. 2.3, Fig. 2/3)

@@ -25,10 +25,14 @@ multi-shift QR/QZ algorithm with aggressive early deflation", ACM TOMS 2021):
                       eigenvalue perturbation theory).
 * ``testmats``     -- matrices with known spectra (Sec. 5.3 syn_n, companion,
                       cyclic, prescribed spectrum).
+* ``qz``           -- the generalized case of the paper's remarks: the
+                      Hessenberg-triangular reduction, double-shift QZ sweeps,
+                      infinite eigenvalues chased to the top of the active
+                      block, standardised 2x2 blocks.
 
 Parity pins (what fixes each function independently of itself) live in
 ``tests/test_oracle_*.py``.  Functions with no independent pin say
 "parity unpinned" in their docstring.
 """
 
-from . import householder, qr, metrics, adjoint, testmats  # noqa: F401
+from . import householder, qr, metrics, adjoint, testmats, qz  # noqa: F401

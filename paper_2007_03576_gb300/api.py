@@ -320,3 +320,67 @@ def eig(A, **schur_kw):
     S, Z, wr, wi, info = schur(H, Q, **schur_kw)
     X = eigenvectors(S, Z, wr, wi)
     return wr, wi, X, info
+
+
+def qz(H, T, Q=None, Z=None, want_qz=True):
+    """Generalized real Schur form of the Hessenberg-triangular pair (H, T):
+    returns (S, T', Q', Z', alphar, alphai, beta, info) with
+    (S, T') = Q'^T (H, T) Z'.  Q, Z given: the transformations are
+    accumulated into copies of them; else they start as the identity.
+    H and T are not modified."""
+    lib = _lib.load()
+    n = H.shape[0]
+    S = colmajor(H.detach())
+    if S.data_ptr() == H.data_ptr():
+        S = S.clone()
+    Tc = colmajor(T.detach())
+    if Tc.data_ptr() == T.data_ptr():
+        Tc = Tc.clone()
+    zinit = 1 if (Q is not None and Z is not None) else 0
+    if want_qz:
+        Qc = colmajor(Q.detach().clone()) if zinit else new_colmajor(n, device=H.device)
+        Zc = colmajor(Z.detach().clone()) if zinit else new_colmajor(n, device=H.device)
+    else:
+        Qc = Zc = None
+    ar = torch.empty(n, dtype=torch.float64, device=H.device)
+    ai = torch.empty_like(ar)
+    be = torch.empty_like(ar)
+    o = _lib.make_opts(_stream_ptr().value, want_z=1 if want_qz else 0, z_init=zinit)
+    rc = lib.schur_qz(n, S.data_ptr(), _ld(S), Tc.data_ptr(), _ld(Tc), Qc.data_ptr() if Qc is not None else None,
+                      _ld(Qc) if Qc is not None else 1, Zc.data_ptr() if Zc is not None else None,
+                      _ld(Zc) if Zc is not None else 1, ar.data_ptr(), ai.data_ptr(), be.data_ptr(), ctypes.byref(o))
+    _check(rc, "schur_qz")
+    return S, Tc, Qc, Zc, ar, ai, be, rc
+
+
+def qz_batched_inplace(Hs, Ts, Qs, Zs, ars, ais, bes, z_init=0):
+    """schur_qz_batched on column-major buffers (in place); returns the list
+    of per-pair statuses."""
+    lib = _lib.load()
+    b = len(Hs)
+    n = (ctypes.c_int * b)(*[h.shape[0] for h in Hs])
+
+    def ptrs(xs):
+        return (ctypes.c_void_p * b)(*[x.data_ptr() for x in xs])
+
+    def lds(xs):
+        return (ctypes.c_int * b)(*[_ld(x) for x in xs])
+
+    info = (ctypes.c_int * b)()
+    o = _lib.make_opts(_stream_ptr().value, z_init=z_init)
+    rc = lib.schur_qz_batched(b, n, ptrs(Hs), lds(Hs), ptrs(Ts), lds(Ts), ptrs(Qs), lds(Qs), ptrs(Zs), lds(Zs),
+                              ptrs(ars), ptrs(ais), ptrs(bes), info, ctypes.byref(o))
+    _check(rc, "schur_qz_batched")
+    return list(info)
+
+
+def qz_sweep(H, T, Q, Z, lo, hi, ssum, sprod):
+    """One double-shift QZ sweep in place on column-major H, T (Q, Z both
+    given or both None)."""
+    lib = _lib.load()
+    n = H.shape[0]
+    o = _lib.make_opts(_stream_ptr().value)
+    rc = lib.schur_qz_sweep(n, H.data_ptr(), _ld(H), T.data_ptr(), _ld(T), Q.data_ptr() if Q is not None else None,
+                            _ld(Q) if Q is not None else 1, Z.data_ptr() if Z is not None else None,
+                            _ld(Z) if Z is not None else 1, lo, hi, float(ssum), float(sprod), ctypes.byref(o))
+    _check(rc, "schur_qz_sweep")

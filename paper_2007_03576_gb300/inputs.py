@@ -10,6 +10,10 @@ arithmetic.  All generators use numpy's PCG64 (``numpy.random.default_rng``).
   form by the oracle for the n = 256 workload).
 * ``batch_sizes(count, lo, hi, seed)`` -- sizes uniform in [lo, hi] for the
   batched and differentiation workloads.
+* ``ht_pair(n, seed, singular=0)`` -- a Hessenberg-triangular pair: H from
+  hessrand, T upper triangular with N(0, 1) above the diagonal and
+  chi(n-i+1) on it (the R factor of a Gaussian matrix's QR); ``singular``
+  diagonal entries of T set to zero (infinite eigenvalues).
 
 Matrices are returned as numpy arrays in row-major (C) order with the
 mathematical layout H[i, j]; ``colmajor_bytes`` gives the column-major
@@ -66,6 +70,20 @@ def batch_sizes(count, lo, hi, seed):
 def batch_hessrand(sizes, seed):
     """List of hessrand matrices, matrix b drawn with seed (seed, b)."""
     return [hessrand(int(n), [seed, b]) for b, n in enumerate(sizes)]
+
+
+def ht_pair(n, seed, singular=0):
+    """(H, T) Hessenberg-triangular; T_ii = sqrt(chi^2(n - i)) (0-based i),
+    N(0, 1) above; the first ``singular`` entries of a seeded choice of
+    diagonal positions are set to zero."""
+    rng = np.random.default_rng(list(np.atleast_1d(seed)) + [7])
+    H = hessrand(n, seed)
+    T = np.triu(rng.standard_normal((n, n)))
+    T[np.arange(n), np.arange(n)] = np.sqrt(rng.chisquare(n - np.arange(n)))
+    if singular:
+        pos = rng.choice(n, size=singular, replace=False)
+        T[pos, pos] = 0.0
+    return H, T
 
 
 def colmajor_bytes(A):

@@ -57,6 +57,12 @@ SCALAR_CASES = [
      {0: [-1], 1: [None], 2: [N - 1, 0], 4: [N - 1]}),
     ("schur_eigenvectors", [N, DEV, N, DEV, N, DEV, DEV, DEV, N],
      {0: [-1], 1: [None], 2: [N - 1], 4: [N - 1], 5: [None], 6: [None], 7: [None], 8: [N - 1]}),
+    ("schur_qz", [N, DEV, N, DEV, N, DEV, N, DEV, N, DEV, DEV, DEV],
+     {0: [-1], 1: [None], 2: [N - 1], 3: [None], 4: [N - 1], 5: [None], 6: [N - 1], 7: [None], 8: [N - 1],
+      9: [None], 10: [None], 11: [None]}),
+    ("schur_qz_sweep", [N, DEV, N, DEV, N, DEV, N, DEV, N, 0, N - 1, 1.0, 2.0],
+     {0: [2], 1: [None], 2: [N - 1], 3: [None], 4: [N - 1], 6: [N - 1], 8: [N - 1], 9: [-1, N - 2],
+      10: [1, N]}),
 ]
 
 
@@ -164,3 +170,22 @@ def test_phase_workspace_sizes():
     assert b.value < with_z - 1000 * 1000 * 8 + 4096
     assert lib.schur_eigenvectors_workspace(-1, 0, ctypes.byref(b)) == -1
     assert lib.schur_eigenvectors_workspace(10, 0, None) == -3
+
+
+def test_qz_batched_rejects_each_bad_argument():
+    lib = _lib.load()
+    b = 2
+    n = (ctypes.c_int * b)(N, N)
+    ptr = (ctypes.c_void_p * b)(4096, 8192)
+    ld = (ctypes.c_int * b)(N, N)
+    info = (ctypes.c_int * b)()
+    valid = [b, n, ptr, ld, ptr, ld, ptr, ld, ptr, ld, ptr, ptr, ptr, info]
+    bad_ld = (ctypes.c_int * b)(N, N - 1)
+    bad_n = (ctypes.c_int * b)(N, 0)
+    bad_ptr = (ctypes.c_void_p * b)(4096, None)
+    cases = {0: [-1], 1: [None, bad_n], 2: [None, bad_ptr], 3: [None, bad_ld], 4: [None, bad_ptr], 5: [None, bad_ld],
+             6: [None, bad_ptr], 7: [None, bad_ld], 8: [None, bad_ptr], 9: [None, bad_ld], 10: [None, bad_ptr],
+             11: [None, bad_ptr], 12: [None, bad_ptr], 13: [None]}
+    for i, bads in cases.items():
+        for bad in bads:
+            _expect(lib.schur_qz_batched, valid + [_opts()], i, bad)
