@@ -26,12 +26,15 @@
 #include <vector>
 
 #include "../../include/schur_gb300.h"
+#include "common.cuh"
 #include "host.h"
 
 namespace {
 
-constexpr int QZ_THREADS = 256;
-constexpr int QZ_WARPS = QZ_THREADS / 32;
+constexpr int QZ_THREADS = 256;        // pairs of order < QZ_BIG_N
+constexpr int QZ_THREADS_BIG = 1024;   // larger pairs: one column / row per thread
+constexpr int QZ_BIG_N = 384;
+constexpr int QZ_WARPS = QZ_THREADS_BIG / 32;
 constexpr double QZ_U = 0x1p-52;
 
 struct QzDesc {
@@ -54,26 +57,6 @@ struct GM {
   long long ld;
   __device__ double& operator()(int r, int c) const { return p[r + c * ld]; }
 };
-
-// Householder reflector of (x0, x1, x2) (nr = 2 or 3), the oracle's
-// convention: beta = -sign(x0) ||x||, tau = (beta - x0) / beta,
-// v = (1, x1, x2) / (x0 - beta); tau = 0 (identity) when the tail is zero.
-__device__ void qz_house(int nr, double x0, double x1, double x2, double& v1, double& v2, double& tau,
-                         double& beta) {
-  const double sigma = (nr == 3) ? hypot(x1, x2) : fabs(x1);
-  if (sigma == 0.0) {
-    v1 = 0.0;
-    v2 = 0.0;
-    tau = 0.0;
-    beta = x0;
-    return;
-  }
-  beta = -copysign(hypot(x0, sigma), x0);
-  tau = (beta - x0) / beta;
-  const double d = x0 - beta;
-  v1 = x1 / d;
-  v2 = (nr == 3) ? x2 / d : 0.0;
-}
 
 // (c, s) of a left rotation of rows (i, k) that zeroes b (the pair (a, b)
 // becomes (hypot(a, b), 0)).
@@ -169,7 +152,7 @@ __device__ double block_sum(double v, QzShared* sh) {
   if ((threadIdx.x & 31) == 0) sh->red[threadIdx.x >> 5] = v;
   __syncthreads();
   double t = 0.0;
-  for (int w = 0; w < QZ_WARPS; ++w) t += sh->red[w];
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh->red[w];
   __syncthreads();
   return t;
 }
@@ -184,7 +167,7 @@ __device__ int block_ireduce(int v, int op, QzShared* sh) {
   if ((threadIdx.x & 31) == 0) sh->ired[threadIdx.x >> 5] = v;
   __syncthreads();
   int t = sh->ired[0];
-  for (int w = 1; w < QZ_WARPS; ++w) t = op ? min(t, sh->ired[w]) : max(t, sh->ired[w]);
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = op ? min(t, sh->ired[w]) : max(t, sh->ired[w]);
   __syncthreads();
   return t;
 }
@@ -385,89 +368,182 @@ __device__ void qz_shifts(const GM& H, const GM& T, int lo, int hi, bool excepti
   sprod = m00 * m11 - m01 * m10;
 }
 
-// one double-shift sweep on lo..hi (the oracle's qz_sweep)
+// left reflector (1, v1, v2) applied to one column's entries (a0, a1, a2):
+// the arithmetic of left_apply, so that thread 0 can predict the values the
+// block writes
+__device__ __forceinline__ void left3_col(double v1, double v2, double tau, double& a0, double& a1, double& a2) {
+  const double s = tau * fma(v2, a2, fma(v1, a1, a0));
+  a0 = fma(-s, 1.0, a0);
+  a1 = fma(-s, v1, a1);
+  a2 = fma(-s, v2, a2);
+}
+
+// one double-shift sweep on lo..hi (the oracle's qz_sweep).  Reflectors come
+// from house3, the short-chain reflector of the standard case: the oracle's
+// convention (beta = -sign(x0) ||x||, tau = (beta - x0) / beta,
+// v = (1, x1, x2) / (x0 - beta), identity for a zero tail), built from FP32
+// seeds and one Newton step instead of IEEE division and square root.  Per
+// position
+// thread 0 builds all three reflectors at once -- the left one from the
+// bulge column, the two right ones from T's 3x3 diagonal block after the
+// left one, computed with the same arithmetic as the block's own updates --
+// so a position costs three block barriers: left products, right products
+// (both right reflectors applied by the thread that owns a row), bookkeeping.
 __device__ void qz_sweep_dev(const GM& H, const GM& T, const GM& Q, const GM& Z, int n, int lo, int hi, double ssum,
                              double sprod, bool wz, QzShared* sh) {
+  double x0 = 0.0, x1 = 0.0, x2 = 0.0;   // the bulge column (thread 0)
   if (threadIdx.x == 0) {
     const double m00 = H(lo, lo) / T(lo, lo), m10 = H(lo + 1, lo) / T(lo, lo);
     const double tl = T(lo, lo + 1), t11 = T(lo + 1, lo + 1);
     const double m01 = (H(lo, lo + 1) - m00 * tl) / t11;
     const double m11 = (H(lo + 1, lo + 1) - m10 * tl) / t11;
     const double m21 = H(lo + 2, lo + 1) / t11;
-    sh->x[0] = m00 * m00 + m10 * m01 - ssum * m00 + sprod;
-    sh->x[1] = m00 * m10 + m10 * m11 - ssum * m10;
-    sh->x[2] = m10 * m21;
+    x0 = m00 * m00 + m10 * m01 - ssum * m00 + sprod;
+    x1 = m00 * m10 + m10 * m11 - ssum * m10;
+    x2 = m10 * m21;
   }
   for (int k = lo; k < hi - 1; ++k) {
     if (threadIdx.x == 0) {
+      if (k > lo) {
+        x0 = H(k, k - 1);
+        x1 = H(k + 1, k - 1);
+        x2 = H(k + 2, k - 1);
+      }
       double v1, v2, tau, beta;
-      qz_house(3, sh->x[0], sh->x[1], sh->x[2], v1, v2, tau, beta);
+      house3(3, x0, x1, x2, v1, v2, tau, beta);
+      // T[k..k+2, k..k+2] after the left reflector (lower part exactly zero)
+      double b00 = T(k, k), b10 = 0.0, b20 = 0.0;
+      double b01 = T(k, k + 1), b11 = T(k + 1, k + 1), b21 = 0.0;
+      double b02 = T(k, k + 2), b12 = T(k + 1, k + 2), b22 = T(k + 2, k + 2);
+      if (tau != 0.0) {
+        left3_col(v1, v2, tau, b00, b10, b20);
+        left3_col(v1, v2, tau, b01, b11, b21);
+        left3_col(v1, v2, tau, b02, b12, b22);
+      }
+      // first right reflector: row k+2 -> (0, 0, *), w = (u2, u1, 1)
+      double u1, u2, t1, g1;
+      house3(3, b22, b21, b20, u1, u2, t1, g1);
+      // its effect on row k+1 (right_apply's arithmetic), then the second
+      // right reflector from (T[k+1, k], T[k+1, k+1]), w = (z1, 1)
+      if (t1 != 0.0) {
+        const double s = t1 * fma(1.0, b12, fma(u1, b11, u2 * b10));
+        b10 = fma(-s, u2, b10);
+        b11 = fma(-s, u1, b11);
+      }
+      double z1, z2, t2, g2;
+      house3(2, b11, b10, 0.0, z1, z2, t2, g2);
       sh->w[0] = v1;
       sh->w[1] = v2;
       sh->w[2] = tau;
       sh->w[3] = beta;
+      sh->m[0] = u2;
+      sh->m[1] = u1;
+      sh->m[2] = t1;
+      sh->m[3] = z1;
+      sh->m[4] = t2;
     }
     __syncthreads();
     {
       const double v1 = sh->w[0], v2 = sh->w[1], tau = sh->w[2];
       const int c0 = (k > lo) ? k - 1 : lo;
-      left_apply(H, k, 3, c0, n, 1.0, v1, v2, tau);
-      left_apply(T, k, 3, k, n, 1.0, v1, v2, tau);
-      if (wz) right_apply(Q, k, 3, 0, n, 1.0, v1, v2, tau);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (k > lo) {
-        H(k, k - 1) = sh->w[3];
-        H(k + 1, k - 1) = 0.0;
-        H(k + 2, k - 1) = 0.0;
+      // H's columns c0..n-1, T's columns k..n-1 and Q's rows in one pass,
+      // so that the three matrices' loads overlap
+      if (tau != 0.0) {
+        const int nh = n - c0, nt = n - k, total = nh + nt + (wz ? n : 0);
+        for (int it = threadIdx.x; it < total; it += blockDim.x) {
+          if (it < nh) {
+            const int c = c0 + it;
+            double a0 = H(k, c), a1 = H(k + 1, c), a2 = H(k + 2, c);
+            left3_col(v1, v2, tau, a0, a1, a2);
+            H(k, c) = a0;
+            H(k + 1, c) = a1;
+            H(k + 2, c) = a2;
+          } else if (it < nh + nt) {
+            const int c = k + (it - nh);
+            double a0 = T(k, c), a1 = T(k + 1, c), a2 = T(k + 2, c);
+            left3_col(v1, v2, tau, a0, a1, a2);
+            T(k, c) = a0;
+            T(k + 1, c) = a1;
+            T(k + 2, c) = a2;
+          } else {
+            const int r = it - nh - nt;
+            double a0 = Q(r, k), a1 = Q(r, k + 1), a2 = Q(r, k + 2);
+            left3_col(v1, v2, tau, a0, a1, a2);
+            Q(r, k) = a0;
+            Q(r, k + 1) = a1;
+            Q(r, k + 2) = a2;
+          }
+        }
       }
-      double v1, v2, tau, beta;
-      qz_house(3, T(k + 2, k + 2), T(k + 2, k + 1), T(k + 2, k), v1, v2, tau, beta);
-      sh->w[0] = v2;   // reversed: w = (v2, v1, 1)
-      sh->w[1] = v1;
-      sh->w[2] = tau;
     }
     __syncthreads();
-    const int rmax = min(k + 3, hi);
+    if (threadIdx.x == 0 && k > lo) {
+      H(k, k - 1) = sh->w[3];
+      H(k + 1, k - 1) = 0.0;
+      H(k + 2, k - 1) = 0.0;
+    }
     {
-      const double w0 = sh->w[0], w1 = sh->w[1], tau = sh->w[2];
-      right_apply(H, k, 3, 0, rmax + 1, w0, w1, 1.0, tau);
-      right_apply(T, k, 3, 0, k + 3, w0, w1, 1.0, tau);
-      if (wz) right_apply(Z, k, 3, 0, n, w0, w1, 1.0, tau);
+      const double a0w = sh->m[0], a1w = sh->m[1], t1 = sh->m[2], z1 = sh->m[3], t2 = sh->m[4];
+      const int rmax = min(k + 3, hi);
+      // one row per thread: the 3x3 reflector on columns k..k+2, then the
+      // 2x2 on columns k, k+1 (rows past k+1 of T get only the first)
+      auto both = [&](const GM& M, int r, bool second) {
+        double e0 = M(r, k), e1 = M(r, k + 1), e2 = M(r, k + 2);
+        if (t1 != 0.0) {
+          const double s = t1 * fma(1.0, e2, fma(a1w, e1, a0w * e0));
+          e0 = fma(-s, a0w, e0);
+          e1 = fma(-s, a1w, e1);
+          e2 = fma(-s, 1.0, e2);
+        }
+        if (second && t2 != 0.0) {
+          const double s = t2 * fma(0.0, 0.0, fma(1.0, e1, z1 * e0));
+          e0 = fma(-s, z1, e0);
+          e1 = fma(-s, 1.0, e1);
+        }
+        M(r, k) = e0;
+        M(r, k + 1) = e1;
+        M(r, k + 2) = e2;
+      };
+      const int nh = rmax + 1, nt = k + 3, total = nh + nt + (wz ? n : 0);
+      for (int it = threadIdx.x; it < total; it += blockDim.x) {
+        if (it < nh)
+          both(H, it, true);
+        else if (it < nh + nt)
+          both(T, it - nh, it - nh <= k + 1);
+        else
+          both(Z, it - nh - nt, true);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       T(k + 2, k) = 0.0;
       T(k + 2, k + 1) = 0.0;
-      double v1, v2, tau, beta;
-      qz_house(2, T(k + 1, k + 1), T(k + 1, k), 0.0, v1, v2, tau, beta);
-      sh->w[0] = v1;   // reversed: w = (v1, 1)
-      sh->w[2] = tau;
-    }
-    __syncthreads();
-    {
-      const double w0 = sh->w[0], tau = sh->w[2];
-      right_apply(H, k, 2, 0, rmax + 1, w0, 1.0, 0.0, tau);
-      right_apply(T, k, 2, 0, k + 2, w0, 1.0, 0.0, tau);
-      if (wz) right_apply(Z, k, 2, 0, n, w0, 1.0, 0.0, tau);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
       T(k + 1, k) = 0.0;
-      sh->x[0] = H(k + 1, k);
-      sh->x[1] = H(k + 2, k);
-      sh->x[2] = (k + 3 <= hi) ? H(k + 3, k) : 0.0;
     }
-    __syncthreads();
   }
+  // last position: rows / columns hi-1, hi
   const int k = hi - 1;
   if (threadIdx.x == 0) {
+    x0 = H(k, k - 1);
+    x1 = H(k + 1, k - 1);
     double v1, v2, tau, beta;
-    qz_house(2, sh->x[0], sh->x[1], 0.0, v1, v2, tau, beta);
+    house3(2, x0, x1, 0.0, v1, v2, tau, beta);
+    double b10 = 0.0, b11 = T(k + 1, k + 1);
+    if (tau != 0.0) {   // column k: (T(k, k), 0); column k+1: (T(k, k+1), T(k+1, k+1))
+      const double a0 = T(k, k), a1 = 0.0;
+      const double s0 = tau * fma(0.0, 0.0, fma(v1, a1, a0));
+      b10 = fma(-s0, v1, a1);
+      const double c0 = T(k, k + 1), c1 = T(k + 1, k + 1);
+      const double s1 = tau * fma(0.0, 0.0, fma(v1, c1, c0));
+      b11 = fma(-s1, v1, c1);
+    }
+    double z1, z2, t2, g2;
+    house3(2, b11, b10, 0.0, z1, z2, t2, g2);
     sh->w[0] = v1;
     sh->w[2] = tau;
     sh->w[3] = beta;
+    sh->m[3] = z1;
+    sh->m[4] = t2;
   }
   __syncthreads();
   {
@@ -480,17 +556,12 @@ __device__ void qz_sweep_dev(const GM& H, const GM& T, const GM& Q, const GM& Z,
   if (threadIdx.x == 0) {
     H(k, k - 1) = sh->w[3];
     H(k + 1, k - 1) = 0.0;
-    double v1, v2, tau, beta;
-    qz_house(2, T(k + 1, k + 1), T(k + 1, k), 0.0, v1, v2, tau, beta);
-    sh->w[0] = v1;
-    sh->w[2] = tau;
   }
-  __syncthreads();
   {
-    const double w0 = sh->w[0], tau = sh->w[2];
-    right_apply(H, k, 2, 0, hi + 1, w0, 1.0, 0.0, tau);
-    right_apply(T, k, 2, 0, k + 2, w0, 1.0, 0.0, tau);
-    if (wz) right_apply(Z, k, 2, 0, n, w0, 1.0, 0.0, tau);
+    const double z1 = sh->m[3], t2 = sh->m[4];
+    right_apply(H, k, 2, 0, hi + 1, z1, 1.0, 0.0, t2);
+    right_apply(T, k, 2, 0, k + 2, z1, 1.0, 0.0, t2);
+    if (wz) right_apply(Z, k, 2, 0, n, z1, 1.0, 0.0, t2);
   }
   __syncthreads();
   if (threadIdx.x == 0) T(k + 1, k) = 0.0;
@@ -606,7 +677,8 @@ __device__ int qz_pair(const QzDesc& d, bool wz, int z_init, QzShared* sh) {
   return info;
 }
 
-__global__ void __launch_bounds__(QZ_THREADS) k_qz(const QzDesc* __restrict__ descs, int batch, int want_z, int z_init,
+template <int NT>
+__global__ void __launch_bounds__(NT) k_qz(const QzDesc* __restrict__ descs, int batch, int want_z, int z_init,
                                                    int* __restrict__ info) {
   __shared__ QzShared sh;
   for (int b = blockIdx.x; b < batch; b += gridDim.x) {
@@ -617,7 +689,7 @@ __global__ void __launch_bounds__(QZ_THREADS) k_qz(const QzDesc* __restrict__ de
 }
 
 // one sweep with given shifts (the single-step parity entry point)
-__global__ void __launch_bounds__(QZ_THREADS) k_qz_sweep(QzDesc d, int lo, int hi, double ssum, double sprod) {
+__global__ void __launch_bounds__(QZ_THREADS_BIG) k_qz_sweep(QzDesc d, int lo, int hi, double ssum, double sprod) {
   __shared__ QzShared sh;
   const GM H{d.H, d.ldh}, T{d.T, d.ldt}, Q{d.Q, d.ldq}, Z{d.Z, d.ldz};
   qz_sweep_dev(H, T, Q, Z, d.n, lo, hi, ssum, sprod, d.Q != nullptr, &sh);
@@ -659,7 +731,12 @@ int run_qz(const std::vector<QzPair>& ps, int* info_out, const schur_opts* opts)
     int* dinfo = (int*)(mem + desc_bytes);
     schur::ck_at(cudaMemcpyAsync(dd, hd.data(), nb * sizeof(QzDesc), cudaMemcpyHostToDevice, st), __LINE__);
     const int grid = std::min(nb, 8 * schur::num_sms());
-    k_qz<<<grid, QZ_THREADS, 0, st>>>(dd, nb, o.want_z, o.z_init, dinfo);
+    int nmax = 0;
+    for (const QzPair& p : ps) nmax = std::max(nmax, p.n);
+    if (nmax >= QZ_BIG_N)
+      k_qz<QZ_THREADS_BIG><<<grid, QZ_THREADS_BIG, 0, st>>>(dd, nb, o.want_z, o.z_init, dinfo);
+    else
+      k_qz<QZ_THREADS><<<grid, QZ_THREADS, 0, st>>>(dd, nb, o.want_z, o.z_init, dinfo);
     schur::ck_at(cudaGetLastError(), __LINE__);
     schur::ck_at(cudaMemcpyAsync(info_out, dinfo, nb * sizeof(int), cudaMemcpyDeviceToHost, st), __LINE__);
     schur::ck_at(cudaStreamSynchronize(st), __LINE__);
@@ -753,7 +830,7 @@ extern "C" int schur_qz_sweep(int n, double* H, int ldh, double* T, int ldt, dou
   schur::read_opts(opts, &o);
   cudaStream_t st = (cudaStream_t)o.stream;
   QzDesc d{H, T, Q, Z, nullptr, nullptr, nullptr, ldh, ldt, Q ? ldq : 1, Z ? ldz : 1, n, 0};
-  k_qz_sweep<<<1, QZ_THREADS, 0, st>>>(d, lo, hi, ssum, sprod);
+  k_qz_sweep<<<1, n >= QZ_BIG_N ? QZ_THREADS_BIG : QZ_THREADS, 0, st>>>(d, lo, hi, ssum, sprod);
   if (cudaGetLastError() != cudaSuccess) return SCHUR_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return SCHUR_ERR_CUDA;
   return SCHUR_OK;
