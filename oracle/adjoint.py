@@ -31,3 +31,90 @@ def eig_adjoint_schur(S, gwr, gwi):
 def eig_adjoint(S, Z, gwr, gwi):
     """dL/dH = Z G_S Z^T."""
     return Z @ eig_adjoint_schur(S, gwr, gwi) @ Z.T
+
+
+# --------------------------------------------------- Schur-factor cotangents
+
+def _block_of(S):
+    n = S.shape[0]
+    blk = np.zeros(n, dtype=int)
+    starts = []
+    j = 0
+    while j < n:
+        starts.append(j)
+        if j + 1 < n and S[j + 1, j] != 0.0:
+            blk[j] = blk[j + 1] = len(starts) - 1
+            j += 2
+        else:
+            blk[j] = len(starts) - 1
+            j += 1
+    return blk, starts
+
+
+def _schur_gauge_system(S):
+    """The linear conditions that fix the first-order change of the real
+    Schur factorisation H = Z S Z^T (not in the paper).  With dZ = Z Omega
+    (Omega skew) and E = Z^T dH Z, the factor changes by
+        dS = E + S Omega - Omega S;
+    Omega's unknowns are its entries below the diagonal outside the 2x2
+    diagonal blocks and the one inside each 2x2 block; the conditions are
+    that dS stays zero below the diagonal blocks and that each 2x2 block stays
+    standardised (equal diagonal entries: d(S_kk - S_k+1,k+1) = 0).
+
+    Returns (unknowns, rows, M) with M the matrix of the conditions applied to
+    S Omega - Omega S for each unknown's Omega = e_i e_j^T - e_j e_i^T, so
+    that the unknowns l solve M l = -cond(E)."""
+    n = S.shape[0]
+    blk, starts = _block_of(S)
+    unknowns = [(i, j) for i in range(n) for j in range(i) if blk[i] != blk[j]]
+    pairs = [k for k in starts if k + 1 < n and blk[k + 1] == blk[k]]
+    unknowns += [(k + 1, k) for k in pairs]
+    rows = [("off", i, j) for (i, j) in unknowns if blk[i] != blk[j]] + [("blk", k, k) for k in pairs]
+
+    def cond(D):
+        return np.array([D[i, j] if kind == "off" else D[i, i] - D[i + 1, i + 1] for kind, i, j in rows])
+
+    M = np.zeros((len(rows), len(unknowns)))
+    for u, (i, j) in enumerate(unknowns):
+        Om = np.zeros((n, n))
+        Om[i, j] = 1.0
+        Om[j, i] = -1.0
+        M[:, u] = cond(S @ Om - Om @ S)
+    return unknowns, rows, M, cond
+
+
+def schur_tangent(S, Z, dH):
+    """(dS, dZ) of the standardised real Schur factors for the perturbation
+    dH, from the conditions of ``_schur_gauge_system`` (dense solve)."""
+    n = S.shape[0]
+    unknowns, rows, M, cond = _schur_gauge_system(S)
+    E = Z.T @ dH @ Z
+    l = -np.linalg.solve(M, cond(E)) if unknowns else np.zeros(0)
+    Om = np.zeros((n, n))
+    for v, (i, j) in zip(l, unknowns):
+        Om[i, j] = v
+        Om[j, i] = -v
+    return E + S @ Om - Om @ S, Z @ Om
+
+
+def schur_factor_adjoint(S, Z, Sbar, Zbar):
+    """dL/dH for a loss L(S, Z) of the standardised real Schur factors with
+    cotangents Sbar = dL/dS, Zbar = dL/dZ: the transpose of
+    ``schur_tangent``.  With G = S^T Sbar - Sbar S^T + Z^T Zbar, the unknowns'
+    cotangents are w_ij = G_ij - G_ji; y = -M^-T w; then
+    Ebar = Sbar + (y placed on the condition rows' entries: E_ij for an
+    off-block row, +E_kk and -E_k+1,k+1 for a block row) and
+    dL/dH = Z Ebar Z^T."""
+    unknowns, rows, M, cond = _schur_gauge_system(S)
+    G = S.T @ Sbar - Sbar @ S.T + Z.T @ Zbar
+    Ebar = np.array(Sbar, dtype=np.float64, copy=True)
+    if unknowns:
+        w = np.array([G[i, j] - G[j, i] for (i, j) in unknowns])
+        y = -np.linalg.solve(M.T, w)
+        for yr, (kind, i, j) in zip(y, rows):
+            if kind == "off":
+                Ebar[i, j] += yr
+            else:
+                Ebar[i, i] += yr
+                Ebar[i + 1, i + 1] -= yr
+    return Z @ Ebar @ Z.T
