@@ -269,6 +269,36 @@ int schur_eig_backward(int n, const double* S, int lds, const double* Z, int ldz
                        const double* wi, const double* gwr, const double* gwi, double* dH, int lddh,
                        const schur_opts* opts);
 
+/*
+ * schur_factor_backward -- adjoint of the Schur factors themselves (not in
+ * the paper): for a real loss L(S, Z) of the standardised factors of
+ * H = Z S Z^T (schur_hessenberg's output), with cotangents Sbar = dL/dS and
+ * Zbar = dL/dZ, returns dL/dH (n x n).  The first-order change of the
+ * factors is dZ = Z Omega (Omega skew), dS = Z^T dH Z + S Omega - Omega S,
+ * with Omega fixed by keeping S quasi-triangular with standardised 2x2 blocks;
+ * the adjoint solves the transposed block-triangular Sylvester system on S
+ * (one thread block, block column by block column) between two sets of FP64
+ * GEMMs.  Requires the diagonal blocks of S to have distinct eigenvalues (the
+ * factors are not differentiable otherwise; a pivot below 2^-52 ||S||_F of a
+ * 2x2 or 4x4 block equation is replaced by that value).  A 2x2 block with
+ * b + c = 0 is invariant under the rotations that keep it standardised; its
+ * rotation term is taken as zero.
+ *   n          order, 0 <= n <= 1024                                (arg 1)
+ *   S, Z       device, the factors (args 2-5); Sbar, Zbar device cotangents
+ *              (args 6-9); dH device output (args 10-11)
+ * Scratch 4 n^2 doubles (+ descriptors), from opts->workspace when set.
+ */
+int schur_factor_backward(int n, const double* S, int lds, const double* Z, int ldz, const double* Sbar, int ldsb,
+                          const double* Zbar, int ldzb, double* dH, int lddh, const schur_opts* opts);
+
+/* schur_factor_backward for `batch` matrices: host arrays of device
+ * pointers and host arrays of ints as in schur_eig_backward_batched; one
+ * thread block per matrix for the Sylvester solve, the GEMMs of all matrices
+ * in shared launches.  A bad argument i returns -i. */
+int schur_factor_backward_batched(int batch, const int* n, double* const* S, const int* lds, double* const* Z,
+                                  const int* ldz, double* const* Sbar, const int* ldsb, double* const* Zbar,
+                                  const int* ldzb, double* const* dH, const int* lddh, const schur_opts* opts);
+
 /* schur_eig_backward for `batch` matrices in one launch sequence; arrays as
  * in schur_hessenberg_batched (host arrays of device pointers; n, lds, ldz
  * and lddh host arrays of ints).  A bad argument i returns -i, also when

@@ -110,6 +110,11 @@ _SIGS = {
     "schur_eigenvectors_workspace": (c_int, [c_int, c_int, P(c_size_t)]),
     "schur_qz": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p,
                          c_void_p, c_void_p, P(SchurOpts)]),
+    "schur_factor_backward": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
+                                      c_void_p, c_int, P(SchurOpts)]),
+    "schur_factor_backward_batched": (c_int, [c_int, P(c_int), P(c_void_p), P(c_int), P(c_void_p), P(c_int),
+                                              P(c_void_p), P(c_int), P(c_void_p), P(c_int), P(c_void_p), P(c_int),
+                                              P(SchurOpts)]),
     "schur_qz_sweep": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_int,
                                c_int, c_double, c_double, P(SchurOpts)]),
     "schur_qz_batched": (c_int, [c_int, P(c_int), P(c_void_p), P(c_int), P(c_void_p), P(c_int), P(c_void_p),

@@ -384,3 +384,70 @@ def qz_sweep(H, T, Q, Z, lo, hi, ssum, sprod):
                             _ld(Q) if Q is not None else 1, Z.data_ptr() if Z is not None else None,
                             _ld(Z) if Z is not None else 1, lo, hi, float(ssum), float(sprod), ctypes.byref(o))
     _check(rc, "schur_qz_sweep")
+
+
+def schur_factor_backward(S, Z, Sbar, Zbar):
+    """dL/dH for a loss L(S, Z) of the standardised Schur factors of H
+    (S, Z from ``schur``), cotangents Sbar = dL/dS, Zbar = dL/dZ."""
+    lib = _lib.load()
+    n = S.shape[0]
+    Sc, Zc = colmajor(S.detach()), colmajor(Z.detach())
+    Sb, Zb = colmajor(Sbar.detach().contiguous().clone()), colmajor(Zbar.detach().contiguous().clone())
+    dH = new_colmajor(n, device=S.device)
+    o = _lib.make_opts(_stream_ptr().value)
+    rc = lib.schur_factor_backward(n, Sc.data_ptr(), _ld(Sc), Zc.data_ptr(), _ld(Zc), Sb.data_ptr(), _ld(Sb),
+                                   Zb.data_ptr(), _ld(Zb), dH.data_ptr(), _ld(dH), ctypes.byref(o))
+    _check(rc, "schur_factor_backward")
+    return dH
+
+
+class SchurFactors(torch.autograd.Function):
+    """(S, Z) = standardised real Schur factors of the upper Hessenberg part
+    of H, with the Schur-factor adjoint as backward (every step in the
+    library).  Entries below the first subdiagonal do not enter the
+    reduction, so their gradient is zero."""
+
+    @staticmethod
+    def forward(ctx, H):
+        S, Z, wr, wi, info = schur(H)
+        if info != 0:
+            raise RuntimeError(f"schur_hessenberg returned {info}")
+        ctx.save_for_backward(S, Z)
+        return S, Z
+
+    @staticmethod
+    def backward(ctx, Sbar, Zbar):
+        S, Z = ctx.saved_tensors
+        if Sbar is None:
+            Sbar = torch.zeros_like(S)
+        if Zbar is None:
+            Zbar = torch.zeros_like(Z)
+        return torch.triu(schur_factor_backward(S, Z, Sbar, Zbar), diagonal=-1)
+
+
+def schur_factors(H):
+    return SchurFactors.apply(H)
+
+
+def schur_factor_backward_batched(Ss, Zs, Sbars, Zbars):
+    """schur_factor_backward for lists of matrices (one launch sequence)."""
+    lib = _lib.load()
+    b = len(Ss)
+    Ss = [colmajor(x.detach()) for x in Ss]
+    Zs = [colmajor(x.detach()) for x in Zs]
+    Sbs = [colmajor(x.detach().contiguous().clone()) for x in Sbars]
+    Zbs = [colmajor(x.detach().contiguous().clone()) for x in Zbars]
+    dHs = [new_colmajor(x.shape[0], device=x.device) for x in Ss]
+
+    def ptrs(xs):
+        return (ctypes.c_void_p * b)(*[x.data_ptr() for x in xs])
+
+    def lds(xs):
+        return (ctypes.c_int * b)(*[_ld(x) for x in xs])
+
+    n = (ctypes.c_int * b)(*[x.shape[0] for x in Ss])
+    o = _lib.make_opts(_stream_ptr().value)
+    rc = lib.schur_factor_backward_batched(b, n, ptrs(Ss), lds(Ss), ptrs(Zs), lds(Zs), ptrs(Sbs), lds(Sbs),
+                                           ptrs(Zbs), lds(Zbs), ptrs(dHs), lds(dHs), ctypes.byref(o))
+    _check(rc, "schur_factor_backward_batched")
+    return dHs

@@ -1,5 +1,5 @@
 // gemm.cuh -- batched FP64 GEMM used by the eigenvector and adjoint entry
-// points: C = alpha * A * op(B) + beta * C, column-major, op(B) = B or B^T.
+// points: C = alpha * op(A) * op(B) + beta * C, column-major, op(X) = X or X^T.
 // Several independent products ("tasks") run in one launch; a block finds its
 // task by binary search over the tasks' first tile index.  Internal linkage:
 // each translation unit that includes it gets its own copy.
@@ -10,8 +10,8 @@
 namespace {
 
 // ---------------------------------------------------------------------------
-// Batched FP64 GEMM: C = alpha * A * op(B) + beta * C (column-major; op(B) =
-// B or B^T), 64 x 64 output tiles, K in chunks of 16 through shared memory,
+// Batched FP64 GEMM: C = alpha * op(A) * op(B) + beta * C (column-major; op(X) =
+// X or X^T), 64 x 64 output tiles, K in chunks of 16 through shared memory,
 // 4 x 4 outputs per thread.
 // ---------------------------------------------------------------------------
 struct GemmTask {
@@ -21,7 +21,7 @@ struct GemmTask {
   long long lda, ldb, ldc;
   int M, N, K, transB;
   double alpha, beta;
-  int tile0, tiles_n, ntile, pad;
+  int tile0, tiles_n, ntile, transA;
 };
 
 __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks, int ntask, int total) {
@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
       for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
         int i = idx & 63, kk = idx >> 6;
         int r = m0 + i, c = k0 + kk;
-        As[kk][i] = (r < t.M && c < t.K) ? t.A[r + (long long)c * t.lda] : 0.0;
+        As[kk][i] = (r < t.M && c < t.K) ? (t.transA ? t.A[c + (long long)r * t.lda] : t.A[r + (long long)c * t.lda])
+                                         : 0.0;
         int j, kb;
         if (t.transB) {
           j = idx & 63;

@@ -57,6 +57,9 @@ SCALAR_CASES = [
      {0: [-1], 1: [None], 2: [N - 1, 0], 4: [N - 1]}),
     ("schur_eigenvectors", [N, DEV, N, DEV, N, DEV, DEV, DEV, N],
      {0: [-1], 1: [None], 2: [N - 1], 4: [N - 1], 5: [None], 6: [None], 7: [None], 8: [N - 1]}),
+    ("schur_factor_backward", [N, DEV, N, DEV, N, DEV, N, DEV, N, DEV, N],
+     {0: [-1, 1025], 1: [None], 2: [N - 1], 3: [None], 4: [N - 1], 5: [None], 6: [N - 1], 7: [None], 8: [N - 1],
+      9: [None], 10: [N - 1]}),
     ("schur_qz", [N, DEV, N, DEV, N, DEV, N, DEV, N, DEV, DEV, DEV],
      {0: [-1], 1: [None], 2: [N - 1], 3: [None], 4: [N - 1], 5: [None], 6: [N - 1], 7: [None], 8: [N - 1],
       9: [None], 10: [None], 11: [None]}),
@@ -189,3 +192,22 @@ def test_qz_batched_rejects_each_bad_argument():
     for i, bads in cases.items():
         for bad in bads:
             _expect(lib.schur_qz_batched, valid + [_opts()], i, bad)
+
+
+def test_factor_backward_batched_rejects_each_bad_argument():
+    lib = _lib.load()
+    b = 2
+    n = (ctypes.c_int * b)(N, N)
+    ptr = (ctypes.c_void_p * b)(4096, 8192)
+    ld = (ctypes.c_int * b)(N, N)
+    valid = [b, n, ptr, ld, ptr, ld, ptr, ld, ptr, ld, ptr, ld]
+    bad_ld = (ctypes.c_int * b)(N, N - 1)
+    bad_n = (ctypes.c_int * b)(N, 1025)
+    bad_ptr = (ctypes.c_void_p * b)(4096, None)
+    cases = {0: [-1], 1: [None, bad_n]}
+    for i in range(2, 12, 2):
+        cases[i] = [None, bad_ptr]
+        cases[i + 1] = [None, bad_ld]
+    for i, bads in cases.items():
+        for bad in bads:
+            _expect(lib.schur_factor_backward_batched, valid + [_opts()], i, bad)
