@@ -51,6 +51,8 @@ def parse():
                     help="skip the batched (4096 x n in [32,768]) and backward (256 x n in [64,1024]) metrics")
     ap.add_argument("--no-checks", action="store_true", help="skip the full-size checks of the last reduction")
     ap.add_argument("--no-cpu-lapack", action="store_true", help="skip the LAPACK (scipy.linalg.schur) CPU sample")
+    ap.add_argument("--split-products", action="store_true",
+                    help="opts.split_products = 1: a chase step's far left products beside the next chase step")
     return ap.parse_args()
 
 
@@ -142,7 +144,8 @@ def bench_config(args, world=1):
           if needs_flush(n) else f"inputs larger than L2 ({size} per matrix), no flush")
     return {"workload": f"hess_n n={n} (Sec. 5.3) Hessenberg -> real Schur, Z accumulated, seed {args.seed}",
             "n": n, "n_shifts": args.ns, "aed_window": args.nw, "deflation": "lapack-style",
-            "l2": l2, "parallelism": f"replicas x{world}"}
+            "l2": l2, "parallelism": f"replicas x{world}",
+            "products": "split over four streams" if getattr(args, "split_products", False) else "three streams"}
 
 
 def reference_arm(args):
@@ -477,7 +480,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     def opts(timing):
-        o = _lib.make_opts(stream.cuda_stream, n_shifts=args.ns, aed_window=args.nw, timing=timing)
+        o = _lib.make_opts(stream.cuda_stream, n_shifts=args.ns, aed_window=args.nw, timing=timing,
+                           split_products=1 if args.split_products else 0)
         o.workspace = ws.data_ptr()
         o.workspace_bytes = ws_bytes
         return o

@@ -93,6 +93,18 @@ typedef struct {
                           active block (LAPACK's rule, which the paper's
                           Sec. 5 names as the source of its shift quality
                           differences); 0 (default): the AED candidates */
+  int split_products;  /* 1: a sweep's left products of each chase step are
+                          split into the columns the next chase step needs
+                          (main stream) and the rest (a fourth stream, beside
+                          the next chase step, with the blocks where another
+                          window's right products meet them); right products
+                          leave those blocks out (schur_sweep_split_tasks
+                          lists the pieces).  Same results up to rounding
+                          order; at n = 20000 on the bench's workload 3 %
+                          faster end to end, with every product launch slower
+                          because more of them overlap.  0 (default): left
+                          products of a step on the main stream, right
+                          products on the side stream */
 } schur_opts;
 
 /* Statistics of the last schur_hessenberg call on this host thread. */
@@ -484,6 +496,20 @@ int schur_fastmath_eval(int n, const double* x, double* out, const schur_opts* o
  *   opts    may be NULL (stream)                                        (arg 5)
  */
 int schur_fp64_fma_probe(int iters, int blocks, double* out, double* flops, const schur_opts* opts);
+
+/*
+ * schur_sweep_split_tasks -- the products of every chase step of a sweep on
+ * rows lo..hi of an n x n H, as the single-matrix path issues them at the
+ * top level with opts.split_products = 1 (host only, no device work).  Record q (8 ints at rec + 8 q):
+ *   step, kind, chain, side, r0, c0, L, nvec
+ * kind 0 near left products (main stream), 1 far left products (far
+ * stream), 2 cross blocks (far stream, after the step's near products),
+ * 3 right products (side stream), 4 Z products; side 0: rows r0..r0+L-1,
+ * columns c0..c0+nvec-1; side 1: rows r0..r0+nvec-1, columns c0..c0+L-1
+ * (kind 4: the rows of Z, nvec = n).  *count = records (all of them, even
+ * when more than cap); rec may be NULL when cap = 0.
+ */
+int schur_sweep_split_tasks(int n, int lo, int hi, int npairs, int bulges_per_chain, int cap, int* rec, int* count);
 
 /*
  * schur_chase_schedule -- the window schedule of one multishift sweep as the

@@ -47,6 +47,7 @@ class SchurOpts(ctypes.Structure):
         ("timing", c_int),
         ("nmin_window", c_int),
         ("recompute_shifts", c_int),
+        ("split_products", c_int),
     ]
 
 
@@ -115,6 +116,7 @@ _SIGS = {
     "schur_factor_backward_batched": (c_int, [c_int, P(c_int), P(c_void_p), P(c_int), P(c_void_p), P(c_int),
                                               P(c_void_p), P(c_int), P(c_void_p), P(c_int), P(c_void_p), P(c_int),
                                               P(SchurOpts)]),
+    "schur_sweep_split_tasks": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, P(c_int), P(c_int)]),
     "schur_qz_sweep": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_int,
                                c_int, c_double, c_double, P(SchurOpts)]),
     "schur_qz_batched": (c_int, [c_int, P(c_int), P(c_void_p), P(c_int), P(c_void_p), P(c_int), P(c_void_p),

@@ -47,7 +47,8 @@ def new_colmajor(n, m=None, device="cuda"):
 
 
 def schur(H, Z=None, *, n_shifts=0, aed_window=0, bulges_per_chain=0, nmin=0, nibble=0, deflation="lapack",
-          fixed_thold=0.0, want_z=True, workspace=None, check=True, nmin_window=0, recompute_shifts=False):
+          fixed_thold=0.0, want_z=True, workspace=None, check=True, nmin_window=0, recompute_shifts=False,
+          split_products=False):
     """Real Schur form of the upper Hessenberg H: returns (S, Z, wr, wi, info)
     with S = Z^T H Z (H itself is not modified).  If Z is given the
     transformations are accumulated into a copy of it (Z <- Z Z_QR); else Z
@@ -67,7 +68,7 @@ def schur(H, Z=None, *, n_shifts=0, aed_window=0, bulges_per_chain=0, nmin=0, ni
     o = _lib.make_opts(_stream_ptr().value, n_shifts=n_shifts, aed_window=aed_window,
                        bulges_per_chain=bulges_per_chain, nmin=nmin, nibble=nibble, deflation=deflation,
                        fixed_thold=fixed_thold, want_z=1 if want_z else 0, z_init=zinit, nmin_window=nmin_window,
-                       recompute_shifts=1 if recompute_shifts else 0)
+                       recompute_shifts=1 if recompute_shifts else 0, split_products=1 if split_products else 0)
     if workspace is not None:
         o.workspace = workspace.data_ptr()
         o.workspace_bytes = workspace.numel() * workspace.element_size()

@@ -306,12 +306,12 @@ Solver::Solver(const schur_opts* o) {
 }
 
 Solver::~Solver() {
-  for (cudaStream_t x : {zst, sst, own_st})
+  for (cudaStream_t x : {zst, sst, fst, own_st})
     if (x) {
       cudaStreamSynchronize(x);
       cudaStreamDestroy(x);
     }
-  for (cudaEvent_t e : {ev_t1, ev_t2, ev_join, ev_base})
+  for (cudaEvent_t e : {ev_t1, ev_t2, ev_join, ev_base, ev_c, ev_n, ev_f})
     if (e) cudaEventDestroy(e);
   for (auto& r : live)
     if (r.ev) cudaEventDestroy(r.ev);
@@ -333,6 +333,10 @@ void Solver::init_streams(bool with_z) {
   // one level below the main stream, so that a chase step's blocks are
   // placed before the side stream's
   ck(cudaStreamCreateWithPriority(&sst, cudaStreamNonBlocking, greatest < least ? greatest + 1 : greatest));
+  ck(cudaStreamCreateWithPriority(&fst, cudaStreamNonBlocking, greatest < least ? greatest + 1 : greatest));
+  ck(cudaEventCreateWithFlags(&ev_c, cudaEventDisableTiming));
+  ck(cudaEventCreateWithFlags(&ev_n, cudaEventDisableTiming));
+  ck(cudaEventCreateWithFlags(&ev_f, cudaEventDisableTiming));
   ust = st;
   ck(cudaEventRecord(ev_join, ust));
   ck(cudaStreamWaitEvent(own_st, ev_join, 0));
@@ -342,9 +346,9 @@ void Solver::init_streams(bool with_z) {
     timer.on = true;
     ck(cudaEventCreate(&ev_base));
     ck(cudaEventRecord(ev_base, st));
-    PhaseTimer* ts[3] = {&timer, &ztimer, &stimer};
-    for (int k = 0; k < 3; ++k) {
-      ts[k]->sid = k;
+    PhaseTimer* ts[4] = {&timer, &ztimer, &stimer, &ftimer};
+    for (int k = 0; k < 4; ++k) {
+      ts[k]->sid = (k == 3) ? 2 : k;
       ts[k]->base = &ev_base;
       ts[k]->trace = &trace;
     }
@@ -352,6 +356,7 @@ void Solver::init_streams(bool with_z) {
     trace_path = nullptr;
   }
   stimer.on = timer.on;
+  ftimer.on = timer.on;
   if (with_z) {
     ck(cudaStreamCreateWithPriority(&zst, cudaStreamNonBlocking, least));
     ck(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
@@ -390,8 +395,9 @@ double* Solver::arena_alloc(size_t n) {
   int last = -1;
   for (size_t i = 0; i < live.size(); ++i)
     if (live[i].a < b && a < live[i].b) last = (int)i;
-  // the side stream may still read the last chase step's region
+  // the side stream (and the far stream) may still read the last chase step's region
   if (t2_pending && t2_a < b && a < t2_b) ck(cudaStreamWaitEvent(st, ev_t2, 0));
+  if (f_pending && f_a < b && a < f_b) ck(cudaStreamWaitEvent(st, ev_f, 0));
   for (int i = 0; i <= last; ++i) {
     Region r = live.front();
     live.pop_front();
@@ -477,6 +483,7 @@ void Solver::read_ctl(const Ctl* dctl) {
   timer.flush();
   if (zst) ztimer.flush_completed();
   if (sst) stimer.flush_completed();
+  if (fst) ftimer.flush_completed();
 }
 
 DeflParams Solver::defl(int n) const {
@@ -493,9 +500,10 @@ static double apply_u_entries(const UpdTask& q, int tn);
 // Issue a list of off-window products (split in launches of at most
 // MAX_UPD_TASKS tasks; tasks within a launch must not overlap).
 void Solver::run_updates(std::vector<UpdTask>& tasks, cudaStream_t sarg, bool on_z) {
-  const bool on_side = !on_z && sarg != nullptr && sarg == sst;
+  const bool on_far = !on_z && sarg != nullptr && sarg == fst;
+  const bool on_side = !on_z && sarg != nullptr && (sarg == sst || on_far);
   cudaStream_t s = (on_z || on_side) ? sarg : st;
-  PhaseTimer& tm = on_z ? ztimer : (on_side ? stimer : timer);
+  PhaseTimer& tm = on_z ? ztimer : (on_far ? ftimer : (on_side ? stimer : timer));
   const int phase = on_z ? PH_Z : cur_update_phase;
   size_t i = 0;
   while (i < tasks.size()) {
@@ -715,6 +723,124 @@ static int chase_launch(const SweepPlan& P, int lo, int hi, int s, ChaseArgs& a)
   return na;
 }
 
+// Products of one chase step on four streams (level 0, opts.split_products).  For each window
+// (rows/columns ws..we, transform U):
+//   near   U^T on rows ws..we, the columns up to the last column of any next-
+//          step window sharing its rows: all the next chase step needs -- on
+//          the main stream;
+//   far    U^T on the remaining columns -- on the far stream, beside the
+//          next chase step;
+//   right  H U on the rows above the window, the rows of the windows above it
+//          left out -- on the side stream;
+//   cross  H U on the rows of each window above it (the blocks where another
+//          window's left products meet this window's right products) -- on
+//          the far stream after that window's near and far products;
+//   Z      as before, deferred to the Z stream.
+// Order between steps: near(s) after far/cross(s-1) and right(s-1) (the rows
+// of a window overlap those of the previous step); far(s) after right(s-1);
+// right(s) after far/cross(s-1).  Right products never meet the next chase
+// step's windows (the schedule is built that way).
+// The products of chase step s as rectangles of H (or Z), by kind:
+// 0 near (main), 1 far (far stream), 2 cross (far stream, after near),
+// 3 right (side stream), 4 Z.  side 0: rows r0..r0+L-1, columns
+// c0..c0+nvec-1; side 1: rows r0..r0+nvec-1, columns c0..c0+L-1.
+struct SplitRect {
+  int kind, chain, side, r0, c0, L, nvec;
+};
+
+static void split_rects(const SweepPlan& plan, int lo, int hi, int s, const ChaseArgs& a, int na, int n, bool with_z,
+                        std::vector<SplitRect>& out) {
+  ChaseArgs an;
+  const int nan = (s + 1 < plan.last) ? chase_launch(plan, lo, hi, s + 1, an) : 0;
+  for (int i = 0; i < na; ++i) {
+    const ChainDesc& d = a.c[i];
+    const int L = d.we - d.ws + 1;
+    auto add = [&](int kind, int side, int r0, int c0, int nvec) {
+      if (nvec > 0) out.push_back(SplitRect{kind, i, side, r0, c0, L, nvec});
+    };
+    // near: up to the last column of any next-step window that shares rows
+    int near_end = d.we;
+    for (int k = 0; k < nan; ++k)
+      if (an.c[k].ws <= d.we && d.ws <= an.c[k].we) near_end = std::max(near_end, an.c[k].we);
+    near_end = std::min(near_end, n - 1);
+    add(0, 0, d.ws, d.we + 1, near_end - d.we);
+    add(1, 0, d.ws, near_end + 1, n - near_end - 1);
+    if (with_z) add(4, 1, 0, d.ws, n);
+    // rows above the window: the gaps between the windows above are right
+    // products, the windows' own rows cross blocks
+    std::vector<std::pair<int, int>> above;
+    for (int j = 0; j < na; ++j)
+      if (a.c[j].we < d.ws) above.push_back({a.c[j].ws, a.c[j].we});
+    std::sort(above.begin(), above.end());
+    int cur = 0;
+    for (auto& w : above) {
+      add(3, 1, cur, d.ws, w.first - cur);
+      add(2, 1, w.first, d.ws, w.second - w.first + 1);
+      cur = w.second + 1;
+    }
+    add(3, 1, cur, d.ws, d.ws - cur);
+  }
+}
+
+void Solver::sweep_step_split(const Mat3& M, const SweepPlan& plan, int lo, int hi, int s, const ChaseArgs& a,
+                              int na, double* ubase, size_t need, bool zasync, bool use_arena) {
+  const int kwin = plan.kwin, delta = plan.delta;
+  std::vector<SplitRect> rects;
+  split_rects(plan, lo, hi, s, a, na, M.n, M.Z != nullptr, rects);
+  std::vector<UpdTask> tn, tf, tx, t2, tz;
+  std::vector<const int2*> hr(na);
+  for (int i = 0; i < na; ++i) {
+    const ChainDesc& d = a.c[i];
+    host_ranges.emplace_back();
+    chase_u_ranges(lo, hi, d.ws, d.we, d.tau0, d.tau1, d.nb, host_ranges.back());
+    hr[i] = host_ranges.back().data();
+  }
+  for (const SplitRect& r : rects) {
+    const ChainDesc& d = a.c[r.chain];
+    const double* U = ubase + d.uoff;
+    std::vector<UpdTask>& v = (r.kind == 0) ? tn : (r.kind == 1) ? tf : (r.kind == 2) ? tx : (r.kind == 3) ? t2
+                              : (zasync ? tz : tf);
+    double* A = (r.kind == 4) ? M.Z : M.H;
+    const long long ld = (r.kind == 4) ? M.ldz : M.ldh;
+    const int nvec = (r.kind == 4) ? M.zrows : r.nvec;
+    v.push_back(make_task(A, ld, r.side, r.r0, r.c0, r.L, nvec, U, kwin, nullptr));
+    set_chase_band(v.back(), d.nb, delta);
+    v.back().rng = (const int2*)(U + (size_t)kwin * kwin);
+    v.back().hrng = hr[r.chain];
+  }
+  if (zasync) z_defer(tz, ubase, need);
+  else if (use_arena) arena_release(ubase, need, false);
+  // main: the next chase step needs only the near products
+  ck(cudaEventRecord(ev_c, st));
+  if (f_pending) ck(cudaStreamWaitEvent(st, ev_f, 0));
+  if (t2_pending) ck(cudaStreamWaitEvent(st, ev_t2, 0));
+  run_updates(tn);
+  ck(cudaEventRecord(ev_n, st));
+  // side: right products after this step's transforms and the previous
+  // far/cross products; far: after this step's transforms and the previous
+  // right products.  (Holding both back until the near products are done
+  // keeps the next chase step's SMs free but leaves the products less time:
+  // measured slower.)
+  ck(cudaStreamWaitEvent(sst, ev_c, 0));
+  if (f_pending) ck(cudaStreamWaitEvent(sst, ev_f, 0));
+  ck(cudaStreamWaitEvent(fst, ev_c, 0));
+  if (t2_pending) ck(cudaStreamWaitEvent(fst, ev_t2, 0));
+  run_updates(tf, fst);
+  if (!tx.empty()) {
+    ck(cudaStreamWaitEvent(fst, ev_n, 0));
+    run_updates(tx, fst);
+  }
+  ck(cudaEventRecord(ev_f, fst));
+  f_pending = true;
+  f_a = use_arena ? (size_t)(ubase - arena) : 0;
+  f_b = use_arena ? f_a + need : 0;
+  run_updates(t2, sst);
+  ck(cudaEventRecord(ev_t2, sst));
+  t2_pending = true;
+  t2_a = f_a;
+  t2_b = f_b;
+}
+
 void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs, int npairs, int nbc_req) {
   Level& Lv = levels[lev];
   const int nbc0 = nbc_req > 0 ? nbc_req : (opts.bulges_per_chain > 0 ? opts.bulges_per_chain : 16);
@@ -741,6 +867,10 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
     g_stats.window_launches += 1;
     if (lev == 0) g_stats.chase_launches += 1;
     count_launches = (lev == 0);
+    if (side && fst && opts.split_products) {
+      sweep_step_split(M, plan, lo, hi, s, a, na, ubase, need, zasync, use_arena);
+      continue;
+    }
     std::vector<UpdTask> t1, t2, tz;
     for (int i = 0; i < na; ++i) {
       const ChainDesc& d = a.c[i];
@@ -797,6 +927,10 @@ void Solver::sweep(const Mat3& M, int lev, int lo, int hi, const double* dpairs,
   if (t2_pending) {
     ck(cudaStreamWaitEvent(st, ev_t2, 0));
     t2_pending = false;
+  }
+  if (f_pending) {
+    ck(cudaStreamWaitEvent(st, ev_f, 0));
+    f_pending = false;
   }
   if (zasync) z_flush();
   host_ranges.clear();   // every task of the sweep has been issued
@@ -1037,11 +1171,12 @@ extern "C" int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, d
     ck(cudaStreamSynchronize(s.st));
     s.timer.flush();
     s.read_ctl(s.levels[0].ctl);
-    for (cudaStream_t x : {s.zst, s.sst})
+    for (cudaStream_t x : {s.zst, s.sst, s.fst})
       if (x) ck(cudaStreamSynchronize(x));
     s.ztimer.flush_completed();
     s.stimer.flush_completed();
-    for (int ph = 0; ph < PH_COUNT; ++ph) s.timer.ms[ph] += s.ztimer.ms[ph] + s.stimer.ms[ph];
+    s.ftimer.flush_completed();
+    for (int ph = 0; ph < PH_COUNT; ++ph) s.timer.ms[ph] += s.ztimer.ms[ph] + s.stimer.ms[ph] + s.ftimer.ms[ph];
     s.write_trace();
     g_stats.aed_cycles_schur = (double)s.hctl->cyc_schur;
     g_stats.shift_recomputations = s.hctl->recomputed;
@@ -1294,6 +1429,43 @@ extern "C" int schur_chase_schedule(int lo, int hi, int npairs, int bulges_per_c
 // ---------------------------------------------------------------------------
 // FP64 FMA throughput probe (the roofline's in-run peak).
 // ---------------------------------------------------------------------------
+extern "C" int schur_sweep_split_tasks(int n, int lo, int hi, int npairs, int bulges_per_chain, int cap, int* rec,
+                                      int* count) {
+  if (n < 1) return -1;
+  if (lo < 0 || lo > n - 1) return -2;
+  if (hi <= lo || hi > n - 1) return -3;
+  if (npairs < 1 || npairs > 1024) return -4;
+  if (bulges_per_chain < 0) return -5;
+  if (cap < 0) return -6;
+  if (cap > 0 && !rec) return -7;
+  if (!count) return -8;
+  const SweepPlan plan = plan_sweep(lo, hi, npairs, bulges_per_chain > 0 ? bulges_per_chain : 16);
+  int cnt = 0;
+  for (int s = 0; s < plan.last; ++s) {
+    ChaseArgs a;
+    const int na = chase_launch(plan, lo, hi, s, a);
+    if (na == 0) continue;
+    std::vector<SplitRect> rects;
+    split_rects(plan, lo, hi, s, a, na, n, true, rects);
+    for (const SplitRect& r : rects) {
+      if (cnt < cap) {
+        int* q = rec + 8 * cnt;
+        q[0] = s;
+        q[1] = r.kind;
+        q[2] = r.chain;
+        q[3] = r.side;
+        q[4] = r.r0;
+        q[5] = r.c0;
+        q[6] = r.L;
+        q[7] = r.nvec;
+      }
+      ++cnt;
+    }
+  }
+  *count = cnt;
+  return SCHUR_OK;
+}
+
 extern "C" int schur_fp64_fma_probe(int iters, int blocks, double* out, double* flops, const schur_opts* opts) {
   if (iters < 1) return -1;
   if (blocks < 1) return -2;

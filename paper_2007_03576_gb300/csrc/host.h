@@ -14,6 +14,7 @@
 
 namespace schur {
 
+
 struct CudaError {
   cudaError_t e;
 };
@@ -95,6 +96,13 @@ struct Solver {
   cudaStream_t ust = nullptr, own_st = nullptr, sst = nullptr;
   PhaseTimer stimer;
   cudaEvent_t ev_t1 = nullptr, ev_t2 = nullptr, ev_join = nullptr;
+  // far-column left products and the cross blocks of a chase step run on
+  // fst beside the next chase step (their timer reports as the side stream)
+  cudaStream_t fst = nullptr;
+  PhaseTimer ftimer;
+  cudaEvent_t ev_c = nullptr, ev_n = nullptr, ev_f = nullptr;
+  bool f_pending = false;
+  size_t f_a = 0, f_b = 0;
   // SCHUR_TRACE=<file>: every timed bracket of the call is written there as
   // "stream,phase,start_ms,end_ms" (streams 0 main, 1 Z, 2 side)
   cudaEvent_t ev_base = nullptr;
@@ -139,6 +147,8 @@ struct Solver {
                              bool with_z = true);
   void z_async(std::vector<UpdTask>& tasks, cudaEvent_t done);   // Z tasks on zst after st's current point
   void z_defer(std::vector<UpdTask>& tasks, const double* p, size_t n);  // held until z_flush
+  void sweep_step_split(const Mat3& M, const struct SweepPlan& plan, int lo, int hi, int s, const ChaseArgs& a,
+                        int na, double* ubase, size_t need, bool zasync, bool use_arena);
   void z_flush();                                                // issue zpending on zst after st's current point
   void drain_z();                                                // st waits for all of zst's work
   void init_streams(bool with_z);                               // see ust / sst / zst

@@ -350,3 +350,15 @@ def test_recompute_shifts_vs_oracle(mode):
                                    stats=st)
     assert st.recomputed > 0
     _eig_match(_np(wr) + 1j * _np(wi), wro + 1j * wio, So, np.linalg.norm(H))
+
+
+def test_split_products_same_result():
+    """opts.split_products = 1 applies the same products to the same entries
+    in the same order per entry (only their grouping into launches and
+    streams changes), so the result equals the default schedule's exactly."""
+    H = inputs.hessrand(1500, 1501)
+    S1, Z1, wr1, wi1, rc1 = api.schur(_dev(H), n_shifts=64, aed_window=96)
+    S2, Z2, wr2, wi2, rc2 = api.schur(_dev(H), n_shifts=64, aed_window=96, split_products=True)
+    assert rc1 == 0 and rc2 == 0
+    assert torch.equal(S1, S2) and torch.equal(Z1, Z2) and torch.equal(wr1, wr2)
+    _check_result(H, _np(S2), _np(Z2))
