@@ -2,7 +2,7 @@
 
 Workload (default): one n = 20000 Hessenberg matrix of the paper's hess_n family
 (Sec. 5.3: N(0,1) on and above the diagonal, chi(n-i) subdiagonal), seed 2023,
-Z accumulated from the identity, 128 shifts, AED window 160, AED repeated
+Z accumulated from the identity, 160 shifts, AED window 160, AED repeated
 above 20 % deflation (tuned settings).  A step is one full reduction S = Z^T H Z
 with the input already resident in HBM (a device copy restores H before each
 step).  The matrix (3.2 GB each for H and Z) is larger than L2, so no flush
@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=20000)
-    ap.add_argument("--ns", type=int, default=128)
+    ap.add_argument("--ns", type=int, default=160)
     ap.add_argument("--nw", type=int, default=160)
     ap.add_argument("--seed", type=int, default=2023)
     ap.add_argument("--no-e2e", action="store_true")
