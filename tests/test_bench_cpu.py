@@ -36,7 +36,7 @@ def _check_line(d, gpus):
     assert d["unit"] == "s" and d["higher_is_better"] is False
     assert d["value"] > 0 and d["ms_per_step"] > 0
     assert d["n_gpus"] == gpus and d["steps"] == 1 and d["warmup"] == 3
-    assert d["config"]["n"] == 20000 and d["config"]["n_shifts"] == 128 and d["config"]["aed_window"] == 160
+    assert d["config"]["n"] == 20000 and d["config"]["n_shifts"] == 160 and d["config"]["aed_window"] == 160 and d["config"]["nibble"] == 20
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
