@@ -273,10 +273,14 @@ def secondary_metrics(api, inputs, torch, np, peak=None):
     tr, _ = timed(lambda: api.hessenberg_reduce(Ad))
     rfl = api.last_stats()["flops"]
     H = inputs.hessrand(n, 2021)
-    S, Z, wr1, wi1, _ = api.schur(torch.from_numpy(np.ascontiguousarray(H.T)).cuda().t())
+    Hd = torch.from_numpy(np.ascontiguousarray(H.T)).cuda().t()
+    tf4, (S, Z, wr1, wi1, _) = timed(lambda: api.schur(Hd))
     api.eigenvectors(S, Z, wr1, wi1)                    # warm-up
     te, _ = timed(lambda: api.eigenvectors(S, Z, wr1, wi1))
     efl = api.last_stats()["flops"]
+    api.eig_backward(S, Z, wr1, wi1, 2 * wr1, -2 * wi1)  # warm-up
+    tb4, _ = timed(lambda: api.eig_backward(S, Z, wr1, wi1, 2 * wr1, -2 * wi1))
+    bfl = api.last_stats()["flops"]
     out["phases_n4096"] = {
         "reduction": {"workload": "dense N(0,1) n=4096 seed 2022 -> H, Q", "seconds": tr,
                       "algorithmic_flops": rfl, "tflops": rfl / tr / 1e12,
@@ -284,7 +288,13 @@ def secondary_metrics(api, inputs, torch, np, peak=None):
         "eigenvectors": {"workload": "hess_n n=4096 seed 2021 Schur form -> X = Z X_S", "seconds": te,
                          "algorithmic_flops": efl, "tflops": efl / te / 1e12,
                          "frac_of_peak": (efl / te / 1e12 / peak) if peak else None},
-        "flops_note": "reduction (10/3 + 4/3) n^3, eigenvectors n^3/3 + n^3 (the counts of the same work in LAPACK)"}
+        "backward": {"workload": "hess_n n=4096 seed 2021, L = sum Re lambda^2 -> dL/dH (blocked vector path)",
+                     "seconds": tb4, "forward_s": tf4, "backward_over_forward": tb4 / tf4,
+                     "algorithmic_flops": bfl, "tflops": bfl / tb4 / 1e12,
+                     "frac_of_peak": (bfl / tb4 / 1e12 / peak) if peak else None},
+        "flops_note": "reduction (10/3 + 4/3) n^3, eigenvectors n^3/3 + n^3 (the counts of the same work in LAPACK); "
+                      "backward: the GEMM flops it issues (two n^3/3 substitutions, about n^3/3 + n^3 + 2 n^3 "
+                      "for Z Re(sum e w x^T) Z^T)"}
     return out
 
 

@@ -266,8 +266,14 @@ int schur_batched_set_table(int nbuckets, const int* max_n, const int* ns, const
  *     G = Re( sum_k conj(g_k) / (y_k^H x_k) * conj(y_k) x_k^T ),
  * x_k, y_k the right / left eigenvectors of S (first-order eigenvalue
  * perturbation: d lambda = y^H dH x / y^H x).  The eigenvectors come from
- * block back / forward substitution on the quasi-triangular S.
- *   n          order, 0 <= n <= 1024                                (arg 1)
+ * block back / forward substitution on the quasi-triangular S: below order
+ * 512 one warp per eigenvalue; from order 512 on the blocked solver of
+ * schur_eigenvectors, run on S and on the reversed transpose of S (whose
+ * right eigenvectors are y reversed), then three FP64 GEMMs that skip the
+ * triangular factors' zeros (about 3.3 n^3 + 2 n^3/3 flops).  A pivot below
+ * a small multiple of u ||S|| (nearly repeated eigenvalues) is replaced by
+ * it.
+ *   n          order, n >= 0                                        (arg 1)
  *   S, lds     device, the standardised Schur factor from schur_hessenberg
  *                                                                (args 2, 3)
  *   Z, ldz     device, the Schur vectors from schur_hessenberg       (args 4, 5)
@@ -276,7 +282,12 @@ int schur_batched_set_table(int nbuckets, const int* max_n, const int* ns, const
  *                                                                (args 8, 9)
  *   dH, lddh   device, output n x n                                  (args 10, 11)
  *   opts       may be NULL (stream, workspace)                        (arg 12)
+ * Scratch: schur_eig_backward_workspace(n) bytes (5 n^2 doubles below order
+ * 512, 3 n^2 above, plus small tables), from opts->workspace when set
+ * (SCHUR_ERR_WORKSPACE if smaller), else allocated for the call.
+ * Synchronises opts->stream before returning.
  */
+int schur_eig_backward_workspace(int n, size_t* bytes);
 int schur_eig_backward(int n, const double* S, int lds, const double* Z, int ldz, const double* wr,
                        const double* wi, const double* gwr, const double* gwi, double* dH, int lddh,
                        const schur_opts* opts);

@@ -87,6 +87,7 @@ _SIGS = {
     "schur_last_error_detail": (ctypes.c_char_p, []),
     "schur_hessenberg_batched": (c_int, [c_int, P(c_int), P(c_void_p), P(c_int), P(c_void_p), P(c_int),
                                          P(c_void_p), P(c_void_p), P(c_int), P(SchurOpts)]),
+    "schur_eig_backward_workspace": (c_int, [c_int, P(c_size_t)]),
     "schur_eig_backward": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_int, P(SchurOpts)]),
     "schur_eig_backward_batched": (c_int, [c_int, P(c_int), P(c_void_p), P(c_int), P(c_void_p), P(c_int),

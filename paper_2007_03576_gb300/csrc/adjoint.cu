@@ -17,6 +17,23 @@
 //     XR = Re x, XI = Im x, P = Re(e w), Q = Im(e w) with e the coefficient
 //     above (zero columns for the second row of a pair).
 //   * k_gemm: G = P XR^T - Q XI^T, T = Z G, dH = T Z^T (FP64 FFMA tiles).
+// That per-warp path serves the batched entry point and single matrices below
+// ADJ_BLOCKED_MIN.  Larger single matrices (any order) take both vector sets
+// from the blocked back substitution of the eigenvector solver (eigvec.cu):
+//   * x_k: the right eigenvectors X of S in LAPACK's real format;
+//   * w_k: with R the reversal permutation (R e_i = e_{n-1-i}),
+//     S' = R S^T R is upper quasi-triangular with the same 2x2 blocks (a
+//     standardised [[a, b], [c, a]] maps to itself), and S^T w = lam w iff
+//     S' (R w) = lam (R w): w_k = R x'_{n-1-k} with x' the right eigenvectors
+//     of S' (a pair (k, k+1) of S sits at (n-2-k, n-1-k) of S', the
+//     eigenvalue with positive imaginary part first: wi' = -R wi);
+//   * k_adj_combine: c_k, e_k and P with G = P X^T (P column k = Re(e w),
+//     column k+1 = -Im(e w) for a pair);
+//   * three GEMM launches that skip the known zeros: P is lower triangular
+//     and X upper triangular up to one entry per pair, so G(i, j) = 0 for
+//     i < j - 2 and its column block J needs only k >= j0 - 1 and, for rows
+//     below i1, k <= i1; T = Z G needs k >= j0 - 2; dH = T Z^T is dense.
+//     About n^3/3 + n^3 + 2 n^3 flops, plus n^3/3 for each vector set.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,7 +47,9 @@
 #include "host.h"
 
 #define ADJ_WARPS 8          // warps (vector blocks) per thread block
-#define ADJ_NMAX 1024
+#define ADJ_NMAX 1024        // largest order of the per-warp path (its shared-memory rows)
+#define ADJ_BLOCKED_MIN 512  // single matrices of this order or more: blocked vectors, any order
+#define ADJ_CH 512           // row chunk of the G = P X^T tasks
 
 struct AdjDesc {
   const double* S;
@@ -295,6 +314,87 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_adj_vectors(const AdjDesc* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// Blocked path, step 1: S' = R S^T R, i.e. S'(i, j) = S(n-1-j, n-1-i), by
+// 32 x 32 tiles through shared memory (both sides coalesced), and
+// wr' = R wr, wi' = -R wi.  Grid (ceil(n/32), ceil(n/32)), 256 threads.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_revT(const double* __restrict__ S, long long lds, int n,
+                                                 double* __restrict__ Sp, const double* __restrict__ wr,
+                                                 const double* __restrict__ wi, double* __restrict__ wrp,
+                                                 double* __restrict__ wip) {
+  __shared__ double tile[32][33];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;   // tile of S': rows i0.., columns j0..
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {                       // tile[r][tx] = S'(i0 + r, j0 + tx)
+    const int i = i0 + r, j = j0 + tx;
+    tile[r][tx] = (i < n && j < n) ? S[(n - 1 - j) + (long long)(n - 1 - i) * lds] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + tx, j = j0 + r;
+    if (i < n && j < n) Sp[i + (long long)j * n] = tile[tx][r];
+  }
+  if (blockIdx.y == 0 && threadIdx.x < 32) {
+    const int i = i0 + threadIdx.x;
+    if (i < n) {
+      const double w = wi[n - 1 - i];
+      wrp[i] = wr[n - 1 - i];
+      wip[i] = (w == 0.0) ? 0.0 : -w;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Blocked path, step 2: one warp per eigenvalue index k (the first of a
+// pair; the second's warp returns).  X, Wp (= the right eigenvectors of S')
+// and P are n x n with leading dimension n.  c = w^T x over the block rows
+// (the only rows where both are nonzero), e = g / c (real) or
+// (conj(g_k) + g_{k+1}) / c (pair); P column k = Re(e w), column k+1 =
+// -Im(e w), so that P X^T = Re(e w x^T).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_combine(const double* __restrict__ X, const double* __restrict__ Wp,
+                                                    const double* __restrict__ wi, const double* __restrict__ gwr,
+                                                    const double* __restrict__ gwi, double* __restrict__ P, int n) {
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (k >= n) return;
+  const double wk = wi[k];
+  if (wk < 0.0) return;
+  const bool pair = wk > 0.0 && k + 1 < n;
+  const long long ln = n;
+  cplx c{0.0, 0.0}, num;
+  if (!pair) {
+    c.r = X[k + k * ln] * Wp[(n - 1 - k) + (n - 1 - k) * ln];
+    num = {gwr[k], 0.0};
+  } else {
+    for (int t = 0; t < 2; ++t) {
+      const int r = k + t;
+      const cplx x{X[r + k * ln], X[r + (k + 1) * ln]};
+      const cplx w{Wp[(n - 1 - r) + (n - 2 - k) * ln], Wp[(n - 1 - r) + (n - 1 - k) * ln]};
+      const cplx p = cmul(w, x);
+      c.r += p.r;
+      c.i += p.i;
+    }
+    num = {gwr[k] + gwr[k + 1], gwi[k + 1] - gwi[k]};
+  }
+  const cplx e = cdiv(num, c, 1e-300);
+  double* p0 = P + k * ln;
+  if (!pair) {
+    const double* wc = Wp + (n - 1 - k) * ln;
+    for (int r = lane; r < n; r += 32) p0[r] = e.r * wc[n - 1 - r];
+  } else {
+    const double* wre = Wp + (n - 2 - k) * ln;
+    const double* wim = Wp + (n - 1 - k) * ln;
+    double* p1 = p0 + ln;
+    for (int r = lane; r < n; r += 32) {
+      const cplx ew = cmul(e, cplx{wre[n - 1 - r], wim[n - 1 - r]});
+      p0[r] = ew.r;
+      p1[r] = -ew.i;
+    }
+  }
+}
+
 // ===========================================================================
 // Host side
 // ===========================================================================
@@ -331,6 +431,15 @@ static void adj_raise_limit() {
   g_adj_done[dev] = true;
 }
 
+size_t warp_path_bytes(const std::vector<int>& ns) {
+  size_t ws_doubles = 0;
+  for (int n : ns) ws_doubles += 5 * (size_t)n * n;
+  const size_t nb = ns.size();
+  size_t desc_bytes = (nb * sizeof(AdjDesc) + 255) & ~(size_t)255;
+  size_t task_bytes = ((size_t)4 * nb * sizeof(GemmTask) + 255) & ~(size_t)255;
+  return ws_doubles * sizeof(double) + desc_bytes + task_bytes;
+}
+
 int run_backward(const std::vector<AdjMatrix>& ms, const schur_opts* opts) {
   schur_opts o;
   schur::read_opts(opts, &o);
@@ -344,8 +453,9 @@ int run_backward(const std::vector<AdjMatrix>& ms, const schur_opts* opts) {
     items += m.n;
   }
   size_t desc_bytes = ((size_t)nb * sizeof(AdjDesc) + 255) & ~(size_t)255;
-  size_t task_bytes = ((size_t)4 * nb * sizeof(GemmTask) + 255) & ~(size_t)255;
-  size_t need = ws_doubles * sizeof(double) + desc_bytes + task_bytes;
+  std::vector<int> ns;
+  for (auto& m : ms) ns.push_back(m.n);
+  const size_t need = warp_path_bytes(ns);
   char* mem = nullptr;
   bool own = false;
   int rc = SCHUR_OK;
@@ -443,12 +553,166 @@ int run_backward(const std::vector<AdjMatrix>& ms, const schur_opts* opts) {
   return rc;
 }
 
+// ----------------------------------------------------------- blocked path
+size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// The GEMM tasks of the blocked path (pointers may be null when only the
+// count is wanted): G = P X^T by (64-column block, ADJ_CH-row chunk), then
+// T = Z G by column block, then dH = T Z^T.  first[0..2] = index of each
+// group's first task; returns the flops.
+double blocked_tasks(int n, const double* P, const double* X, double* G, const double* Z, long long ldz, double* T,
+                     double* dH, long long lddh, std::vector<GemmTask>* tasks, int first[3]) {
+  double flops = 0.0;
+  const long long ln = n;
+  auto add = [&](const double* A, long long lda, const double* B, long long ldb, int transB, double* C,
+                 long long ldc, int M, int N, int K) {
+    GemmTask t;
+    memset(&t, 0, sizeof(t));
+    t.A = A; t.B = B; t.C = C; t.lda = lda; t.ldb = ldb; t.ldc = ldc;
+    t.M = M; t.N = N; t.K = K; t.transB = transB; t.alpha = 1.0; t.beta = 0.0;
+    t.tiles_n = (N + 63) / 64;
+    t.ntile = ((M + 63) / 64) * t.tiles_n;
+    tasks->push_back(t);
+    flops += 2.0 * M * (double)N * K;
+  };
+  first[0] = (int)tasks->size();
+  for (int j0 = 0; j0 < n; j0 += 64) {
+    const int j1 = std::min(n, j0 + 64);
+    const int k0 = std::max(0, j0 - 1);
+    for (int i0 = std::max(0, j0 - 2); i0 < n; i0 += ADJ_CH) {
+      const int i1 = std::min(n, i0 + ADJ_CH);
+      const int k1 = std::min(n, i1 + 1);
+      add(P ? P + i0 + k0 * ln : nullptr, ln, X ? X + j0 + k0 * ln : nullptr, ln, 1, G ? G + i0 + j0 * ln : nullptr,
+          ln, i1 - i0, j1 - j0, k1 - k0);
+    }
+  }
+  first[1] = (int)tasks->size();
+  for (int j0 = 0; j0 < n; j0 += 64) {
+    const int j1 = std::min(n, j0 + 64);
+    const int k0 = std::max(0, j0 - 2);
+    add(Z ? Z + k0 * ldz : nullptr, ldz, G ? G + k0 + j0 * ln : nullptr, ln, 0, T ? T + j0 * ln : nullptr, ln, n,
+        j1 - j0, n - k0);
+  }
+  first[2] = (int)tasks->size();
+  add(T, ln, Z, ldz, 1, dH, lddh, n, n, n);
+  return flops;
+}
+
+struct BlockedLayout {
+  size_t buf0, buf1, buf2, wrp, wip, ev, task, total;
+  int ntask;
+};
+
+BlockedLayout blocked_layout(int n) {
+  BlockedLayout L;
+  const size_t nn = al256((size_t)n * n * sizeof(double));
+  const size_t vec = al256((size_t)n * sizeof(double));
+  std::vector<GemmTask> tk;
+  int first[3];
+  blocked_tasks(n, nullptr, nullptr, nullptr, nullptr, n, nullptr, nullptr, n, &tk, first);
+  L.ntask = (int)tk.size();
+  L.buf0 = 0;
+  L.buf1 = nn;
+  L.buf2 = 2 * nn;
+  L.wrp = 3 * nn;
+  L.wip = L.wrp + vec;
+  L.ev = L.wip + vec;
+  L.task = L.ev + al256(schur::eigvec_workspace(n, false));
+  L.total = L.task + al256((size_t)L.ntask * sizeof(GemmTask));
+  return L;
+}
+
+int run_backward_blocked(const AdjMatrix& m, const schur_opts* opts) {
+  schur_opts o;
+  schur::read_opts(opts, &o);
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const int n = m.n;
+  const BlockedLayout L = blocked_layout(n);
+  char* mem = nullptr;
+  bool own = false;
+  if (o.workspace) {
+    if (o.workspace_bytes < L.total) return SCHUR_ERR_WORKSPACE;
+    mem = (char*)o.workspace;
+  } else {
+    if (cudaMalloc((void**)&mem, L.total) != cudaSuccess) {
+      cudaGetLastError();
+      return SCHUR_ERR_NOMEM;
+    }
+    own = true;
+  }
+  int rc = SCHUR_OK;
+  try {
+    schur::init_kernel_attributes();
+    double* b0 = (double*)(mem + L.buf0);   // S', then X
+    double* b1 = (double*)(mem + L.buf1);   // W' (vectors of S'), then G
+    double* b2 = (double*)(mem + L.buf2);   // P, then T
+    double* wrp = (double*)(mem + L.wrp);
+    double* wip = (double*)(mem + L.wip);
+    GemmTask* dtask = (GemmTask*)(mem + L.task);
+    long long launches = 0;
+    double flops = 0.0;
+    std::vector<double> hwi(n), hwip(n);
+    ck_at(cudaMemcpyAsync(hwi.data(), m.wi, n * sizeof(double), cudaMemcpyDeviceToHost, st), __LINE__);
+    ck_at(cudaStreamSynchronize(st), __LINE__);
+    for (int i = 0; i < n; ++i) hwip[i] = (hwi[n - 1 - i] == 0.0) ? 0.0 : -hwi[n - 1 - i];
+    const int nt = (n + 31) / 32;
+    k_adj_revT<<<dim3(nt, nt), 256, 0, st>>>(m.S, m.lds, n, b0, m.wr, m.wi, wrp, wip);
+    ck_at(cudaGetLastError(), __LINE__);
+    ++launches;
+    schur::eigvec_run(n, b0, n, nullptr, 0, wrp, wip, hwip.data(), b1, n, st, mem + L.ev, &launches, &flops);
+    schur::eigvec_run(n, m.S, m.lds, nullptr, 0, m.wr, m.wi, hwi.data(), b0, n, st, mem + L.ev, &launches, &flops);
+    k_adj_combine<<<(n + 7) / 8, 256, 0, st>>>(b0, b1, m.wi, m.gwr, m.gwi, b2, n);
+    ck_at(cudaGetLastError(), __LINE__);
+    ++launches;
+    std::vector<GemmTask> tasks;
+    int first[3];
+    // T overwrites P, which the G launch has finished reading
+    flops += blocked_tasks(n, b2, b0, b1, m.Z, m.ldz, b2, m.dH, m.lddh, &tasks, first);
+    if ((int)tasks.size() != L.ntask) throw CudaError{cudaErrorInvalidValue};
+    // one launch per group (G, then T, then dH: each reads the previous
+    // one's output); tile indices count from 0 within a group
+    const int bounds[4] = {first[0], first[1], first[2], (int)tasks.size()};
+    int ntile[3];
+    for (int g = 0; g < 3; ++g) {
+      int tile = 0;
+      for (int i = bounds[g]; i < bounds[g + 1]; ++i) {
+        tasks[i].tile0 = tile;
+        tile += tasks[i].ntile;
+      }
+      ntile[g] = tile;
+    }
+    ck_at(cudaMemcpyAsync(dtask, tasks.data(), tasks.size() * sizeof(GemmTask), cudaMemcpyHostToDevice, st),
+          __LINE__);
+    ck_at(cudaMemsetAsync(b1, 0, (size_t)n * n * sizeof(double), st), __LINE__);   // G's known zeros
+    const int nsm = schur::num_sms();
+    for (int g = 0; g < 3; ++g) {
+      k_gemm<<<std::min(ntile[g], 4 * nsm), 256, 0, st>>>(dtask + bounds[g], bounds[g + 1] - bounds[g], ntile[g]);
+      ck_at(cudaGetLastError(), __LINE__);
+      ++launches;
+    }
+    ck_at(cudaStreamSynchronize(st), __LINE__);
+    schur::g_stats.kernel_launches = launches;
+    schur::g_stats.flops = flops;
+  } catch (const CudaError&) {
+    rc = SCHUR_ERR_CUDA;
+  }
+  if (own && mem) cudaFree(mem);
+  return rc;
+}
+
 }  // namespace
+
+extern "C" int schur_eig_backward_workspace(int n, size_t* bytes) {
+  if (n < 0) return -1;
+  if (!bytes) return -2;
+  *bytes = (n >= ADJ_BLOCKED_MIN) ? blocked_layout(n).total : warp_path_bytes({std::max(n, 1)});
+  return SCHUR_OK;
+}
 
 extern "C" int schur_eig_backward(int n, const double* S, int lds, const double* Z, int ldz, const double* wr,
                                   const double* wi, const double* gwr, const double* gwi, double* dH, int lddh,
                                   const schur_opts* opts) {
-  if (n < 0 || n > ADJ_NMAX) return -1;
+  if (n < 0) return -1;
   if (n == 0) return SCHUR_OK;
   if (!S) return -2;
   if (lds < n) return -3;
@@ -460,8 +724,10 @@ extern "C" int schur_eig_backward(int n, const double* S, int lds, const double*
   if (!gwi) return -9;
   if (!dH) return -10;
   if (lddh < n) return -11;
-  std::vector<AdjMatrix> ms{AdjMatrix{n, S, Z, wr, wi, gwr, gwi, dH, lds, ldz, lddh}};
-  return run_backward(ms, opts);
+  memset(&schur::g_stats, 0, sizeof(schur::g_stats));
+  const AdjMatrix m{n, S, Z, wr, wi, gwr, gwi, dH, lds, ldz, lddh};
+  if (n >= ADJ_BLOCKED_MIN) return run_backward_blocked(m, opts);
+  return run_backward(std::vector<AdjMatrix>{m}, opts);
 }
 
 extern "C" int schur_eig_backward_batched(int batch, const int* n, double* const* S, const int* lds, double* const* Z,

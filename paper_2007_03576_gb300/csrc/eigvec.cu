@@ -276,6 +276,113 @@ extern "C" int schur_eigenvectors_workspace(int n, int with_z, size_t* bytes) {
   return SCHUR_OK;
 }
 
+namespace schur {
+
+size_t eigvec_workspace(int n, bool with_z) { return workspace_need(std::max(n, 1), with_z); }
+
+// The body of schur_eigenvectors on stream st with scratch `mem`
+// (eigvec_workspace(n, Z != nullptr) bytes); hwi is a host copy of wi (the
+// pair structure).  Does not synchronise; adds its launches and GEMM flops.
+void eigvec_run(int n, const double* S, int lds, const double* Z, int ldz, const double* wr, const double* wi,
+                const double* hwi, double* X, int ldx, cudaStream_t st, char* mem, long long* launches,
+                double* flops) {
+  const bool bt = Z != nullptr;
+  char* p = mem;
+  double* XS = X;
+  long long ldxs = ldx;
+  if (bt) {
+    XS = (double*)p;
+    ldxs = n;
+    p += ((size_t)n * n * sizeof(double) + 255) / 256 * 256;
+  }
+  GemmTask* dtask = (GemmTask*)p;
+  p += tasks_bytes(n);
+  double* part = (double*)p;
+  double* smin = part + EV_FRO_BLOCKS;
+  const int nsm = num_sms();
+  ev_raise_limit();
+
+  std::vector<int> starts;   // block starts, bottom block first
+  for (int k1 = n; k1 > 0;) {
+    int k0 = std::max(0, k1 - EV_B);
+    if (k0 > 0 && hwi[k0 - 1] > 0.0) --k0;   // keep the pair (k0 - 1, k0) together
+    starts.push_back(k0);
+    k1 = k0;
+  }
+
+  // every GEMM task of the call, uploaded once
+  std::vector<GemmTask> tasks;
+  auto task = [&](const double* A, long long lda, const double* Bm, long long ldb, double* C, long long ldc, int M,
+                  int N, int K, double alpha, double beta) {
+    GemmTask tk;
+    memset(&tk, 0, sizeof(tk));
+    tk.A = A; tk.B = Bm; tk.C = C; tk.lda = lda; tk.ldb = ldb; tk.ldc = ldc;
+    tk.M = M; tk.N = N; tk.K = K; tk.transB = 0; tk.alpha = alpha; tk.beta = beta;
+    tk.tiles_n = (N + 63) / 64;
+    tk.ntile = ((M + 63) / 64) * tk.tiles_n;
+    tasks.push_back(tk);
+  };
+  int k1 = n;
+  std::vector<int> sub_task(starts.size(), -1);
+  for (size_t bi = 0; bi < starts.size(); ++bi) {
+    const int k0 = starts[bi];
+    if (k0 > 0) {
+      sub_task[bi] = (int)tasks.size();
+      task(S + (long long)k0 * lds, lds, XS + k0 + (long long)k0 * ldxs, ldxs, XS + (long long)k0 * ldxs, ldxs, k0,
+           n - k0, k1 - k0, -1.0, 1.0);
+      *flops += 2.0 * k0 * (double)(n - k0) * (k1 - k0);
+    }
+    k1 = k0;
+  }
+  const int bt_first = (int)tasks.size();
+  if (bt) {
+    int tile = 0;
+    for (int c0 = 0; c0 < n; c0 += 64) {
+      const int c1 = std::min(n, c0 + 64);
+      const int K = std::min(n, c1 + 1);
+      task(Z, ldz, XS + (long long)c0 * ldxs, ldxs, X + (long long)c0 * ldx, ldx, n, c1 - c0, K, 1.0, 0.0);
+      tasks.back().tile0 = tile;
+      tile += tasks.back().ntile;
+      *flops += 2.0 * n * (double)(c1 - c0) * K;
+    }
+  }
+  if (!tasks.empty())
+    ck_at(cudaMemcpyAsync(dtask, tasks.data(), tasks.size() * sizeof(GemmTask), cudaMemcpyHostToDevice, st),
+          __LINE__);
+
+  // XS = 0 (entries below each eigenvector's block stay zero)
+  ck_at(cudaMemset2DAsync(XS, ldxs * sizeof(double), 0, n * sizeof(double), n, st), __LINE__);
+  k_ev_fro<<<EV_FRO_BLOCKS, 256, 0, st>>>(S, lds, n, part);
+  k_ev_smin<<<1, 32, 0, st>>>(part, EV_FRO_BLOCKS, smin);
+  *launches += 2;
+  k1 = n;
+  for (size_t bi = 0; bi < starts.size(); ++bi) {
+    const int k0 = starts[bi];
+    const int cols = n - k0;
+    const size_t smem = ((size_t)(k1 - k0) * (k1 - k0) + 2 * (size_t)(k1 - k0) * EV_T) * sizeof(double);
+    k_ev_diag<<<(cols + EV_T - 1) / EV_T, EV_T, smem, st>>>(S, lds, wr, wi, XS, ldxs, n, k0, k1, smin);
+    ++*launches;
+    if (sub_task[bi] >= 0) {
+      const GemmTask& tk = tasks[sub_task[bi]];
+      k_gemm<<<std::min(tk.ntile, 4 * nsm), 256, 0, st>>>(dtask + sub_task[bi], 1, tk.ntile);
+      ++*launches;
+    }
+    k1 = k0;
+  }
+  ck_at(cudaGetLastError(), __LINE__);
+  k_ev_norm<<<std::min((n + 7) / 8, 8 * nsm), 256, 0, st>>>(XS, ldxs, wi, n);
+  ++*launches;
+  if (bt) {
+    int total = 0;
+    for (size_t i = bt_first; i < tasks.size(); ++i) total += tasks[i].ntile;
+    k_gemm<<<std::min(total, 4 * nsm), 256, 0, st>>>(dtask + bt_first, (int)tasks.size() - bt_first, total);
+    ++*launches;
+  }
+  ck_at(cudaGetLastError(), __LINE__);
+}
+
+}  // namespace schur
+
 extern "C" int schur_eigenvectors(int n, const double* S, int lds, const double* Z, int ldz, const double* wr,
                                   const double* wi, double* X, int ldx, const schur_opts* opts) {
   if (n < 0) return -1;
@@ -291,8 +398,7 @@ extern "C" int schur_eigenvectors(int n, const double* S, int lds, const double*
   schur_opts o;
   schur::read_opts(opts, &o);
   cudaStream_t st = (cudaStream_t)o.stream;
-  const bool bt = Z != nullptr;
-  const size_t need = workspace_need(n, bt);
+  const size_t need = workspace_need(n, Z != nullptr);
   char* mem = nullptr;
   bool own = false;
   if (o.workspace) {
@@ -307,104 +413,13 @@ extern "C" int schur_eigenvectors(int n, const double* S, int lds, const double*
   }
   int rc = SCHUR_OK;
   try {
-    char* p = mem;
-    double* XS = X;
-    long long ldxs = ldx;
-    if (bt) {
-      XS = (double*)p;
-      ldxs = n;
-      p += ((size_t)n * n * sizeof(double) + 255) / 256 * 256;
-    }
-    GemmTask* dtask = (GemmTask*)p;
-    p += tasks_bytes(n);
-    double* part = (double*)p;
-    double* smin = part + EV_FRO_BLOCKS;
-    long long launches = 0;
-    const int nsm = schur::num_sms();
-    ev_raise_limit();
-
     // pair structure (host copy of wi) for the block rows
     std::vector<double> hwi(n);
     ck_at(cudaMemcpyAsync(hwi.data(), wi, n * sizeof(double), cudaMemcpyDeviceToHost, st), __LINE__);
     ck_at(cudaStreamSynchronize(st), __LINE__);
-    std::vector<int> starts;   // block starts, bottom block first
-    for (int k1 = n; k1 > 0;) {
-      int k0 = std::max(0, k1 - EV_B);
-      if (k0 > 0 && hwi[k0 - 1] > 0.0) --k0;   // keep the pair (k0 - 1, k0) together
-      starts.push_back(k0);
-      k1 = k0;
-    }
-
-    // every GEMM task of the call, uploaded once
-    std::vector<GemmTask> tasks;
-    auto task = [&](const double* A, long long lda, const double* Bm, long long ldb, double* C, long long ldc, int M,
-                    int N, int K, double alpha, double beta) {
-      GemmTask tk;
-      memset(&tk, 0, sizeof(tk));
-      tk.A = A; tk.B = Bm; tk.C = C; tk.lda = lda; tk.ldb = ldb; tk.ldc = ldc;
-      tk.M = M; tk.N = N; tk.K = K; tk.transB = 0; tk.alpha = alpha; tk.beta = beta;
-      tk.tiles_n = (N + 63) / 64;
-      tk.ntile = ((M + 63) / 64) * tk.tiles_n;
-      tasks.push_back(tk);
-    };
+    long long launches = 0;
     double flops = 0.0;
-    int k1 = n;
-    std::vector<int> sub_task(starts.size(), -1);
-    for (size_t bi = 0; bi < starts.size(); ++bi) {
-      const int k0 = starts[bi];
-      if (k0 > 0) {
-        sub_task[bi] = (int)tasks.size();
-        task(S + (long long)k0 * lds, lds, XS + k0 + (long long)k0 * ldxs, ldxs, XS + (long long)k0 * ldxs, ldxs, k0,
-             n - k0, k1 - k0, -1.0, 1.0);
-        flops += 2.0 * k0 * (double)(n - k0) * (k1 - k0);
-      }
-      k1 = k0;
-    }
-    const int bt_first = (int)tasks.size();
-    if (bt) {
-      int tile = 0;
-      for (int c0 = 0; c0 < n; c0 += 64) {
-        const int c1 = std::min(n, c0 + 64);
-        const int K = std::min(n, c1 + 1);
-        task(Z, ldz, XS + (long long)c0 * ldxs, ldxs, X + (long long)c0 * ldx, ldx, n, c1 - c0, K, 1.0, 0.0);
-        tasks.back().tile0 = tile;
-        tile += tasks.back().ntile;
-        flops += 2.0 * n * (double)(c1 - c0) * K;
-      }
-    }
-    if (!tasks.empty())
-      ck_at(cudaMemcpyAsync(dtask, tasks.data(), tasks.size() * sizeof(GemmTask), cudaMemcpyHostToDevice, st),
-            __LINE__);
-
-    // XS = 0 (entries below each eigenvector's block stay zero)
-    ck_at(cudaMemset2DAsync(XS, ldxs * sizeof(double), 0, n * sizeof(double), n, st), __LINE__);
-    k_ev_fro<<<EV_FRO_BLOCKS, 256, 0, st>>>(S, lds, n, part);
-    k_ev_smin<<<1, 32, 0, st>>>(part, EV_FRO_BLOCKS, smin);
-    launches += 2;
-    k1 = n;
-    for (size_t bi = 0; bi < starts.size(); ++bi) {
-      const int k0 = starts[bi];
-      const int cols = n - k0;
-      const size_t smem = ((size_t)(k1 - k0) * (k1 - k0) + 2 * (size_t)(k1 - k0) * EV_T) * sizeof(double);
-      k_ev_diag<<<(cols + EV_T - 1) / EV_T, EV_T, smem, st>>>(S, lds, wr, wi, XS, ldxs, n, k0, k1, smin);
-      ++launches;
-      if (sub_task[bi] >= 0) {
-        const GemmTask& tk = tasks[sub_task[bi]];
-        k_gemm<<<std::min(tk.ntile, 4 * nsm), 256, 0, st>>>(dtask + sub_task[bi], 1, tk.ntile);
-        ++launches;
-      }
-      k1 = k0;
-    }
-    ck_at(cudaGetLastError(), __LINE__);
-    k_ev_norm<<<std::min((n + 7) / 8, 8 * nsm), 256, 0, st>>>(XS, ldxs, wi, n);
-    ++launches;
-    if (bt) {
-      int total = 0;
-      for (size_t i = bt_first; i < tasks.size(); ++i) total += tasks[i].ntile;
-      k_gemm<<<std::min(total, 4 * nsm), 256, 0, st>>>(dtask + bt_first, (int)tasks.size() - bt_first, total);
-      ++launches;
-    }
-    ck_at(cudaGetLastError(), __LINE__);
+    schur::eigvec_run(n, S, lds, Z, ldz, wr, wi, hwi.data(), X, ldx, st, mem, &launches, &flops);
     ck_at(cudaStreamSynchronize(st), __LINE__);
     schur::g_stats.kernel_launches = launches;
     schur::g_stats.flops = flops;

@@ -170,4 +170,14 @@ void default_ns_nw(int m, int* ns, int* nw);
 size_t workspace_bytes(int n, const schur_opts& o);
 const char* status_string(int code);
 
+// Right eigenvectors of a standardised quasi-triangular S, the work of
+// schur_eigenvectors (eigvec.cu), on stream st: scratch `mem` of
+// eigvec_workspace(n, Z != nullptr) bytes, hwi a host copy of wi (the pair
+// structure).  Does not synchronise; adds its launches and GEMM flops to
+// *launches / *flops; throws CudaError.
+size_t eigvec_workspace(int n, bool with_z);
+void eigvec_run(int n, const double* S, int lds, const double* Z, int ldz, const double* wr, const double* wi,
+                const double* hwi, double* X, int ldx, cudaStream_t st, char* mem, long long* launches,
+                double* flops);
+
 }  // namespace schur

@@ -33,7 +33,7 @@ SCALAR_CASES = [
     ("schur_hessenberg_noalloc", [N, DEV, N, DEV, N, DEV, DEV],
      {0: [-1], 1: [None], 2: [N - 1], 3: [None], 4: [N - 1], 5: [None], 6: [None]}),
     ("schur_eig_backward", [N, DEV, N, DEV, N, DEV, DEV, DEV, DEV, DEV, N],
-     {0: [-1, 1025], 1: [None], 2: [N - 1], 3: [None], 4: [N - 1], 5: [None], 6: [None], 7: [None],
+     {0: [-1], 1: [None], 2: [N - 1], 3: [None], 4: [N - 1], 5: [None], 6: [None], 7: [None],
       8: [None], 9: [None], 10: [N - 1]}),
     ("schur_sweep", [N, DEV, N, DEV, N, 0, N - 1, (ctypes.c_double * 4)(), 2, 0],
      {0: [0], 1: [None], 2: [N - 1], 4: [N - 1], 5: [-1, N], 6: [1, N], 7: [None], 8: [0, 32 * 32 + 1]}),
@@ -173,6 +173,29 @@ def test_phase_workspace_sizes():
     assert b.value < with_z - 1000 * 1000 * 8 + 4096
     assert lib.schur_eigenvectors_workspace(-1, 0, ctypes.byref(b)) == -1
     assert lib.schur_eigenvectors_workspace(10, 0, None) == -3
+
+
+def test_eig_backward_workspace_and_large_orders():
+    """The eigenvalue adjoint's scratch: five n x n buffers on the per-warp
+    path (orders below 512), three on the blocked path (512 and above, any
+    order); a caller workspace below that size is refused before any device
+    work, at an order the per-warp path could not take."""
+    lib = _lib.load()
+    b = ctypes.c_size_t(0)
+    assert lib.schur_eig_backward_workspace(511, ctypes.byref(b)) == 0
+    assert 5 * 511 * 511 * 8 <= b.value < 5 * 511 * 511 * 8 + 64 * 1024
+    for n in (512, 1500, 20000):
+        assert lib.schur_eig_backward_workspace(n, ctypes.byref(b)) == 0
+        assert 3 * n * n * 8 <= b.value < 3 * n * n * 8 + 8 * 1024 * 1024, (n, b.value)
+    assert lib.schur_eig_backward_workspace(-1, ctypes.byref(b)) == -1
+    assert lib.schur_eig_backward_workspace(10, None) == -2
+    n = 3000
+    assert lib.schur_eig_backward_workspace(n, ctypes.byref(b)) == 0
+    o = _lib.make_opts(0)
+    o.workspace = DEV
+    o.workspace_bytes = b.value - 1
+    rc = lib.schur_eig_backward(n, DEV, n, DEV, n, DEV, DEV, DEV, DEV, DEV, n, ctypes.byref(o))
+    assert rc == _lib.SCHUR_ERR_WORKSPACE
 
 
 def test_qz_batched_rejects_each_bad_argument():

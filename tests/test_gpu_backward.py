@@ -1,5 +1,8 @@
 """Eigenvalue adjoint (backward) on the GPU vs the oracle's adjoint, closed
-forms and central finite differences.
+forms and central finite differences.  Orders below 512 take the per-warp
+vector path, 512 and above the blocked one (both are compared with the
+oracle, and with each other through the batched entry point, which always
+takes the per-warp path).
 
 The adjoint of eigenvalue i scales with its condition number; parity with
 the oracle is asserted entrywise on the same Schur factor (both evaluate
@@ -20,7 +23,7 @@ def _dev(A):
     return torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.float64).T)).cuda().t()
 
 
-@pytest.mark.parametrize("n", [2, 7, 50, 130])
+@pytest.mark.parametrize("n", [2, 7, 50, 130, 511, 512, 700])
 def test_backward_matches_oracle_adjoint(n):
     H = inputs.hessrand(n, 600 + n)
     S, Z, wr, wi, info = api.schur(_dev(H))
@@ -83,3 +86,22 @@ def test_backward_batched_matches_single():
     for s, z, a, b, c, d, dh in zip(S, Z, wr, wi, gr, gi, dHs):
         one = api.eig_backward(s, z, a, b, c, d)
         assert torch.max(torch.abs(one - dh)).item() <= 1e-12 * max(1.0, torch.max(torch.abs(one)).item())
+
+
+@pytest.mark.parametrize("n", [512, 900])
+def test_backward_blocked_matches_warp_path(n):
+    """The two vector paths on the same factors: the single-matrix entry
+    point (blocked, n >= 512) against the batched one (per warp) with one
+    matrix, within 1e-10 * max_i kappa_i * ||g||."""
+    H = inputs.hessrand(n, 900 + n)
+    S, Z, wr, wi, info = api.schur(_dev(H))
+    assert info == 0
+    rng = np.random.default_rng(n)
+    gr = torch.from_numpy(rng.standard_normal(n)).cuda()
+    gi = torch.from_numpy(rng.standard_normal(n)).cuda()
+    one = api.eig_backward(S, Z, wr, wi, gr, gi)
+    (two,) = api.eig_backward_batched([S], [Z], [wr], [wi], [gr], [gi])
+    _, kap = metrics.eig_condition(S.cpu().numpy())
+    scale = np.max(kap) * float(torch.linalg.norm(torch.cat([gr, gi])))
+    err = torch.max(torch.abs(one - two)).item()
+    assert err <= 1e-10 * scale, err / scale
