@@ -7,6 +7,7 @@ import math
 
 import numpy as np
 import pytest
+import scipy.linalg
 
 torch = pytest.importorskip("torch")
 
@@ -44,7 +45,10 @@ def test_batched_mixed_sizes_vs_oracle():
 
 def test_batched_large_members_invariants():
     """Members up to the workload's largest size (768): residual,
-    orthogonality, structure and the trace invariants."""
+    orthogonality, structure and the trace invariants; the eigenvalues
+    against LAPACK's dgeev (library cross-check, scipy) within
+    1e-10 kappa_i ||H||_F, kappa_i from LAPACK's left and right vectors, and
+    the 300-row member against the oracle as well."""
     sizes = [768, 500, 300, 640, 200]
     Hs = [inputs.hessrand(n, [5, i]) for i, n in enumerate(sizes)]
     S, Z, wr, wi, info = api.schur_batched([_dev(h) for h in Hs])
@@ -56,6 +60,15 @@ def test_batched_large_members_invariants():
         nh = np.linalg.norm(h)
         assert abs(np.sum(lam) - np.trace(h)) < 1e-12 * n * nh
         assert abs(np.sum(lam ** 2) - np.trace(h @ h)) < 1e-12 * n * nh ** 2
+        w, vl, vr = scipy.linalg.eig(h, left=True, right=True)
+        kap = np.linalg.norm(vl, axis=0) * np.linalg.norm(vr, axis=0) / np.abs(np.sum(np.conj(vl) * vr, axis=0))
+        perm, dist = metrics.match_eigenvalues(w, lam)
+        assert np.all(dist <= 1e-10 * kap * nh), float(np.max(dist / (kap * nh)))
+        if n == 300:
+            So, Zo, wro, wio, _ = qr.schur(h)
+            _, kap_o = metrics.eig_condition(So)
+            perm, dist = metrics.match_eigenvalues(wro + 1j * wio, lam)
+            assert np.all(dist <= 1e-10 * kap_o * nh)
 
 
 def test_batched_matches_single_path():
