@@ -266,8 +266,8 @@ int schur_batched_set_table(int nbuckets, const int* max_n, const int* ns, const
  *     G = Re( sum_k conj(g_k) / (y_k^H x_k) * conj(y_k) x_k^T ),
  * x_k, y_k the right / left eigenvectors of S (first-order eigenvalue
  * perturbation: d lambda = y^H dH x / y^H x).  The eigenvectors come from
- * block back / forward substitution on the quasi-triangular S: below order
- * 512 one warp per eigenvalue; from order 512 on the blocked solver of
+ * block back / forward substitution on the quasi-triangular S: up to order
+ * 1024 one warp per eigenvalue; above that the blocked solver of
  * schur_eigenvectors, run on S and on the reversed transpose of S (whose
  * right eigenvectors are y reversed), then three FP64 GEMMs that skip the
  * triangular factors' zeros (about 3.3 n^3 + 2 n^3/3 flops).  A pivot below
@@ -282,8 +282,8 @@ int schur_batched_set_table(int nbuckets, const int* max_n, const int* ns, const
  *                                                                (args 8, 9)
  *   dH, lddh   device, output n x n                                  (args 10, 11)
  *   opts       may be NULL (stream, workspace)                        (arg 12)
- * Scratch: schur_eig_backward_workspace(n) bytes (5 n^2 doubles below order
- * 512, 3 n^2 above, plus small tables), from opts->workspace when set
+ * Scratch: schur_eig_backward_workspace(n) bytes (5 n^2 doubles up to order
+ * 1024, 3 n^2 above, plus small tables), from opts->workspace when set
  * (SCHUR_ERR_WORKSPACE if smaller), else allocated for the call.
  * Synchronises opts->stream before returning.
  */
@@ -390,6 +390,37 @@ int schur_eigenvectors_workspace(int n, int with_z, size_t* bytes);
  * the generalized real Schur form (S, T) = Q^T (H, T0) Z of a
  * Hessenberg-triangular pair, by the double-shift QZ iteration.
  * --------------------------------------------------------------------- */
+
+/*
+ * schur_ht_reduce -- Hessenberg-triangular reduction of a general pair (the
+ * generalized case's first phase, Sec. 1 remark): (A, B) -> (H, R) with H
+ * upper Hessenberg and R upper triangular, A = Q H Z^T and B = Q R Z^T.  A
+ * Householder QR of B applied to A, then Givens rotations that zero A below
+ * its subdiagonal column by column from the bottom, each followed by the
+ * right rotation that removes its fill-in in R (Golub & Van Loan Alg. 7.7.1;
+ * the order of the oracle's reduction).  One thread block per pair; the
+ * result is schur_qz's input.
+ *   n          order, n >= 0                                        (arg 1)
+ *   A, lda     device, overwritten by H (zeros below the subdiagonal) (args 2, 3)
+ *   B, ldb     device, overwritten by R (zeros below the diagonal)  (args 4, 5)
+ *   Q, ldq     device n x n: set to the left transformation (I on entry
+ *              unless opts->z_init == 1, then multiplied in place)  (args 6, 7)
+ *   Z, ldz     device n x n: the right transformation, the same way (args 8, 9)
+ *              (Q and Z are not referenced when opts->want_z == 0)
+ *   opts       may be NULL                                         (arg 10)
+ * Returns SCHUR_OK, SCHUR_ERR_NONFINITE (a NaN or Inf in A or B: nothing
+ * changed), or an error code.  Synchronises opts->stream before returning.
+ */
+int schur_ht_reduce(int n, double* A, int lda, double* B, int ldb, double* Q, int ldq, double* Z, int ldz,
+                    const schur_opts* opts);
+
+/* schur_ht_reduce for `batch` pairs in one launch (one thread block per
+ * pair): host arrays of device pointers and of ints as in
+ * schur_qz_batched; info[b] is the per-pair status.  A bad argument i
+ * returns -i. */
+int schur_ht_reduce_batched(int batch, const int* n, double* const* A, const int* lda, double* const* B,
+                            const int* ldb, double* const* Q, const int* ldq, double* const* Z, const int* ldz,
+                            int* info, const schur_opts* opts);
 
 /*
  * schur_qz -- (H, T) upper Hessenberg / upper triangular (n x n, device)

@@ -110,6 +110,10 @@ _SIGS = {
     "schur_eigenvectors": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int,
                                    P(SchurOpts)]),
     "schur_eigenvectors_workspace": (c_int, [c_int, c_int, P(c_size_t)]),
+    "schur_ht_reduce": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
+                                P(SchurOpts)]),
+    "schur_ht_reduce_batched": (c_int, [c_int, P(c_int), P(c_void_p), P(c_int), P(c_void_p), P(c_int),
+                                        P(c_void_p), P(c_int), P(c_void_p), P(c_int), P(c_int), P(SchurOpts)]),
     "schur_qz": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p,
                          c_void_p, c_void_p, P(SchurOpts)]),
     "schur_factor_backward": (c_int, [c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,

@@ -323,6 +323,66 @@ def eig(A, **schur_kw):
     return wr, wi, X, info
 
 
+def ht_reduce(A, B, Q=None, Z=None, want_qz=True):
+    """Hessenberg-triangular reduction of a general pair on the GPU (the
+    generalized case's first phase): returns (H, R, Q', Z') with
+    (A, B) = Q' (H, R) Z'^T, H upper Hessenberg, R upper triangular.  Q, Z
+    given: the transformations are multiplied into copies of them; else they
+    start as the identity.  A and B are not modified."""
+    lib = _lib.load()
+    n = A.shape[0]
+    H = colmajor(A.detach())
+    if H.data_ptr() == A.data_ptr():
+        H = H.clone()
+    R = colmajor(B.detach())
+    if R.data_ptr() == B.data_ptr():
+        R = R.clone()
+    zinit = 1 if (Q is not None and Z is not None) else 0
+    if want_qz:
+        Qc = colmajor(Q.detach().clone()) if zinit else new_colmajor(n, device=A.device)
+        Zc = colmajor(Z.detach().clone()) if zinit else new_colmajor(n, device=A.device)
+    else:
+        Qc = Zc = None
+    o = _lib.make_opts(_stream_ptr().value, want_z=1 if want_qz else 0, z_init=zinit)
+    rc = lib.schur_ht_reduce(n, H.data_ptr(), _ld(H), R.data_ptr(), _ld(R),
+                             Qc.data_ptr() if Qc is not None else None, _ld(Qc) if Qc is not None else 1,
+                             Zc.data_ptr() if Zc is not None else None, _ld(Zc) if Zc is not None else 1,
+                             ctypes.byref(o))
+    _check(rc, "schur_ht_reduce")
+    return H, R, Qc, Zc
+
+
+def ht_reduce_batched_inplace(As, Bs, Qs, Zs, z_init=0):
+    """schur_ht_reduce_batched on column-major buffers (in place); returns
+    the list of per-pair statuses."""
+    lib = _lib.load()
+    b = len(As)
+    n = (ctypes.c_int * b)(*[a.shape[0] for a in As])
+
+    def ptrs(xs):
+        return (ctypes.c_void_p * b)(*[x.data_ptr() for x in xs])
+
+    def lds(xs):
+        return (ctypes.c_int * b)(*[_ld(x) for x in xs])
+
+    info = (ctypes.c_int * b)()
+    o = _lib.make_opts(_stream_ptr().value, z_init=z_init)
+    rc = lib.schur_ht_reduce_batched(b, n, ptrs(As), lds(As), ptrs(Bs), lds(Bs), ptrs(Qs), lds(Qs), ptrs(Zs),
+                                     lds(Zs), info, ctypes.byref(o))
+    _check(rc, "schur_ht_reduce_batched")
+    return list(info)
+
+
+def generalized_schur(A, B, want_qz=True):
+    """Generalized real Schur form of a general pair (A, B) on the GPU:
+    ht_reduce, then qz.  Returns (S, T, Q, Z, alphar, alphai, beta, info)
+    with (A, B) = Q (S, T) Z^T (Q, Z None when want_qz is False)."""
+    H, R, Q, Z = ht_reduce(A, B, want_qz=want_qz)
+    if not want_qz:
+        return qz(H, R, want_qz=False)
+    return qz(H, R, Q, Z)
+
+
 def qz(H, T, Q=None, Z=None, want_qz=True):
     """Generalized real Schur form of the Hessenberg-triangular pair (H, T):
     returns (S, T', Q', Z', alphar, alphai, beta, info) with

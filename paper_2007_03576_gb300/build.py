@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libschur_gb300.so")
-SOURCES = ["kernels.cu", "driver.cu", "batched.cu", "adjoint.cu", "noalloc.cu", "hessred.cu", "eigvec.cu", "qz.cu", "sfadj.cu"]
+SOURCES = ["kernels.cu", "driver.cu", "batched.cu", "adjoint.cu", "noalloc.cu", "hessred.cu", "eigvec.cu", "qz.cu", "sfadj.cu", "htred.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -18,7 +18,10 @@
 //     above (zero columns for the second row of a pair).
 //   * k_gemm: G = P XR^T - Q XI^T, T = Z G, dH = T Z^T (FP64 FFMA tiles).
 // That per-warp path serves the batched entry point and single matrices below
-// ADJ_BLOCKED_MIN.  Larger single matrices (any order) take both vector sets
+// ADJ_BLOCKED_MIN (where it is also the faster one: 4.3 / 6.9 / 13.9 ms against
+// 10.7 / 15.4 / 21.7 ms at n = 512 / 768 / 1024 on a GB300, the blocked path's
+// launches and serial block rows dominating there).  Larger single matrices
+// (any order) take both vector sets
 // from the blocked back substitution of the eigenvector solver (eigvec.cu):
 //   * x_k: the right eigenvectors X of S in LAPACK's real format;
 //   * w_k: with R the reversal permutation (R e_i = e_{n-1-i}),
@@ -48,7 +51,7 @@
 
 #define ADJ_WARPS 8          // warps (vector blocks) per thread block
 #define ADJ_NMAX 1024        // largest order of the per-warp path (its shared-memory rows)
-#define ADJ_BLOCKED_MIN 512  // single matrices of this order or more: blocked vectors, any order
+#define ADJ_BLOCKED_MIN 1025 // single matrices of this order or more: blocked vectors, any order
 #define ADJ_CH 512           // row chunk of the G = P X^T tasks
 
 struct AdjDesc {

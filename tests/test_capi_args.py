@@ -63,6 +63,8 @@ SCALAR_CASES = [
     ("schur_qz", [N, DEV, N, DEV, N, DEV, N, DEV, N, DEV, DEV, DEV],
      {0: [-1], 1: [None], 2: [N - 1], 3: [None], 4: [N - 1], 5: [None], 6: [N - 1], 7: [None], 8: [N - 1],
       9: [None], 10: [None], 11: [None]}),
+    ("schur_ht_reduce", [N, DEV, N, DEV, N, DEV, N, DEV, N],
+     {0: [-1], 1: [None], 2: [N - 1, 0], 3: [None], 4: [N - 1], 5: [None], 6: [N - 1], 7: [None], 8: [N - 1]}),
     ("schur_qz_sweep", [N, DEV, N, DEV, N, DEV, N, DEV, N, 0, N - 1, 1.0, 2.0],
      {0: [2], 1: [None], 2: [N - 1], 3: [None], 4: [N - 1], 6: [N - 1], 8: [N - 1], 9: [-1, N - 2],
       10: [1, N]}),
@@ -177,14 +179,15 @@ def test_phase_workspace_sizes():
 
 def test_eig_backward_workspace_and_large_orders():
     """The eigenvalue adjoint's scratch: five n x n buffers on the per-warp
-    path (orders below 512), three on the blocked path (512 and above, any
-    order); a caller workspace below that size is refused before any device
-    work, at an order the per-warp path could not take."""
+    path (orders up to 1024), three on the blocked path (above, any order);
+    a caller workspace below that size is refused before any device work, at
+    an order the per-warp path could not take."""
     lib = _lib.load()
     b = ctypes.c_size_t(0)
-    assert lib.schur_eig_backward_workspace(511, ctypes.byref(b)) == 0
-    assert 5 * 511 * 511 * 8 <= b.value < 5 * 511 * 511 * 8 + 64 * 1024
-    for n in (512, 1500, 20000):
+    for n in (1, 511, 1024):
+        assert lib.schur_eig_backward_workspace(n, ctypes.byref(b)) == 0
+        assert 5 * n * n * 8 <= b.value < 5 * n * n * 8 + 64 * 1024
+    for n in (1025, 1500, 20000):
         assert lib.schur_eig_backward_workspace(n, ctypes.byref(b)) == 0
         assert 3 * n * n * 8 <= b.value < 3 * n * n * 8 + 8 * 1024 * 1024, (n, b.value)
     assert lib.schur_eig_backward_workspace(-1, ctypes.byref(b)) == -1
@@ -215,6 +218,24 @@ def test_qz_batched_rejects_each_bad_argument():
     for i, bads in cases.items():
         for bad in bads:
             _expect(lib.schur_qz_batched, valid + [_opts()], i, bad)
+
+
+def test_ht_reduce_batched_rejects_each_bad_argument():
+    lib = _lib.load()
+    b = 2
+    n = (ctypes.c_int * b)(N, N)
+    ptr = (ctypes.c_void_p * b)(4096, 8192)
+    ld = (ctypes.c_int * b)(N, N)
+    info = (ctypes.c_int * b)()
+    valid = [b, n, ptr, ld, ptr, ld, ptr, ld, ptr, ld, info]
+    bad_ld = (ctypes.c_int * b)(N, N - 1)
+    bad_n = (ctypes.c_int * b)(N, 0)
+    bad_ptr = (ctypes.c_void_p * b)(4096, None)
+    cases = {0: [-1], 1: [None, bad_n], 2: [None, bad_ptr], 3: [None, bad_ld], 4: [None, bad_ptr], 5: [None, bad_ld],
+             6: [None, bad_ptr], 7: [None, bad_ld], 8: [None, bad_ptr], 9: [None, bad_ld], 10: [None]}
+    for i, bads in cases.items():
+        for bad in bads:
+            _expect(lib.schur_ht_reduce_batched, valid + [_opts()], i, bad)
 
 
 def test_factor_backward_batched_rejects_each_bad_argument():
