@@ -1134,7 +1134,9 @@ extern "C" int schur_hessenberg(int n, double* H, int ldh, double* Z, int ldz, d
   if (n < 0) return -1;
   if (n > 0 && H == nullptr) return -2;
   if (ldh < std::max(1, n)) return -3;
-  int want_z = opts ? opts->want_z : 1;
+  schur_opts oq;
+  schur::read_opts(opts, &oq);
+  int want_z = oq.want_z;
   if (want_z && n > 0 && Z == nullptr) return -4;
   if (want_z && ldz < std::max(1, n)) return -5;
   if (n > 0 && wr == nullptr) return -6;

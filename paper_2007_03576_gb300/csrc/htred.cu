@@ -340,7 +340,9 @@ extern "C" int schur_ht_reduce(int n, double* A, int lda, double* B, int ldb, do
   if (lda < std::max(1, n)) return -3;
   if (n > 0 && B == nullptr) return -4;
   if (ldb < std::max(1, n)) return -5;
-  const int want_qz = opts ? opts->want_z : 1;
+  schur_opts oq;
+  schur::read_opts(opts, &oq);
+  const int want_qz = oq.want_z;
   if (want_qz && n > 0 && Q == nullptr) return -6;
   if (want_qz && ldq < std::max(1, n)) return -7;
   if (want_qz && n > 0 && Z == nullptr) return -8;
@@ -364,7 +366,9 @@ extern "C" int schur_ht_reduce_batched(int batch, const int* n, double* const* A
   if (!lda) return -4;
   if (!B) return -5;
   if (!ldb) return -6;
-  const int want_qz = opts ? opts->want_z : 1;
+  schur_opts oq;
+  schur::read_opts(opts, &oq);
+  const int want_qz = oq.want_z;
   if (want_qz && !Q) return -7;
   if (want_qz && !ldq) return -8;
   if (want_qz && !Z) return -9;

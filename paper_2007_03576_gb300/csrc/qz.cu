@@ -757,7 +757,9 @@ extern "C" int schur_qz(int n, double* H, int ldh, double* T, int ldt, double* Q
   if (ldh < std::max(1, n)) return -3;
   if (n > 0 && T == nullptr) return -4;
   if (ldt < std::max(1, n)) return -5;
-  const int want_z = opts ? opts->want_z : 1;
+  schur_opts oq;
+  schur::read_opts(opts, &oq);
+  const int want_z = oq.want_z;
   if (want_z && n > 0 && Q == nullptr) return -6;
   if (want_z && ldq < std::max(1, n)) return -7;
   if (want_z && n > 0 && Z == nullptr) return -8;
@@ -784,7 +786,9 @@ extern "C" int schur_qz_batched(int batch, const int* n, double* const* H, const
   if (!ldh) return -4;
   if (!T) return -5;
   if (!ldt) return -6;
-  const int want_z = opts ? opts->want_z : 1;
+  schur_opts oq;
+  schur::read_opts(opts, &oq);
+  const int want_z = oq.want_z;
   if (want_z && !Q) return -7;
   if (want_z && !ldq) return -8;
   if (want_z && !Z) return -9;

@@ -255,3 +255,18 @@ def test_factor_backward_batched_rejects_each_bad_argument():
     for i, bads in cases.items():
         for bad in bads:
             _expect(lib.schur_factor_backward_batched, valid + [_opts()], i, bad)
+
+
+def test_short_opts_struct_keeps_defaults_beyond_its_size():
+    """An opts block whose struct_size ends before want_z: the library reads
+    only struct_size bytes, so want_z keeps its default (1) whatever the
+    memory after it holds, and a missing Z / Q is rejected as a bad
+    argument, before any device work (every entry point reads opts through
+    the same reader)."""
+    lib = _lib.load()
+    o = _lib.make_opts(0, want_z=0)
+    o.struct_size = _lib.SchurOpts.want_z.offset
+    ob = ctypes.byref(o)
+    assert lib.schur_hessenberg(N, DEV, N, None, N, DEV, DEV, ob) == -4
+    assert lib.schur_qz(N, DEV, N, DEV, N, None, N, None, N, DEV, DEV, DEV, ob) == -6
+    assert lib.schur_ht_reduce(N, DEV, N, DEV, N, None, N, None, N, ob) == -6
