@@ -1349,7 +1349,9 @@ extern "C" int schur_fastmath_eval(int n, const double* x, double* out, const sc
   if (n > 0 && !x) return -2;
   if (n > 0 && !out) return -3;
   if (n == 0) return SCHUR_OK;
-  cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
+  schur_opts o;
+  read_opts(opts, &o);
+  cudaStream_t st = (cudaStream_t)o.stream;
   k_fastmath_eval<<<std::min((n + 255) / 256, 1024), 256, 0, st>>>(n, x, out);
   if (cudaGetLastError() != cudaSuccess) return SCHUR_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return SCHUR_ERR_CUDA;
