@@ -17,13 +17,15 @@
 //     entry, so no overflow or underflow), v overwrites B's column below the
 //     diagonal, then one warp per column applies the reflector to B and A and
 //     one thread per row to Q;
-//   * stage 2: thread 0 builds the rotation pair from five entries
-//     (A[i-1, j], A[i, j], R[i-1, i-1], R[i-1, i], R[i, i]) into shared
-//     memory, a barrier, then the two rotations are applied in one pass: the left one
-//     to rows i-1, i of A and R outside columns i-1, i, the right one to
-//     columns i-1, i of A, R and Z outside rows i-1, i, Q's columns by the
-//     left one, and the 2x2 blocks of A and R (touched by both) by one thread,
-//     left rotation first; a second barrier ends the step.
+//   * stage 2: the rotation pair of a step comes from five entries
+//     (A[i-1, j], A[i, j], R[i-1, i-1], R[i-1, i], R[i, i]); thread 0 builds
+//     the next step's pair while the other threads apply the current one in
+//     one pass: the left rotation to rows i-1, i of A and R outside columns
+//     i-1, i, the right one to columns i-1, i of A, R and Z outside rows
+//     i-1, i (and outside R's row i-2), Q's columns by the left one.  Thread 0
+//     applies both to the 2x2 blocks of A and R (left first) and the right
+//     one to R's row i-2, which gives it every input of the next pair; one
+//     barrier per step.
 // About n^2 / 2 rotation steps of O(n) work each: a latency-bound kernel
 // meant for batches of small and medium pairs (one SM per pair).
 #include <cuda_runtime.h>
@@ -94,8 +96,26 @@ __device__ __forceinline__ void ht_rot_first(double a, double b, double& c, doub
   s = -a / r;
 }
 
+// The rotation pair of one step from A[i-1, j] = a, A[i, j] = b and R's
+// block (r11, r12; 0, r22): the left rotation zeroing b, then the right one
+// zeroing the fill-in f21 it leaves in R.  out = (c1, s1, c2, s2, f21, f22).
+__device__ __forceinline__ void ht_build_pair(double a, double b, double r11, double r12, double r22,
+                                              double* out) {
+  double c1, s1, c2, s2;
+  ht_rot_second(a, b, c1, s1);
+  const double f21 = -s1 * r11, f22 = fma(-s1, r12, c1 * r22);   // R[i, i-1], R[i, i] after the left rotation
+  ht_rot_first(f21, f22, c2, s2);
+  out[0] = c1;
+  out[1] = s1;
+  out[2] = c2;
+  out[3] = s2;
+  out[4] = f21;
+  out[5] = f22;
+}
+
 template <int NT>
-__device__ void ht_pair(const HtDesc& d, bool want_qz, int z_init, int* info_b, double* red, double* rot) {
+__device__ void ht_pair(const HtDesc& d, bool want_qz, int z_init, int* info_b, double* red,
+                        double (*rotb)[8]) {
   const int n = d.n;
   const GMat A{d.A, d.lda}, B{d.B, d.ldb}, Q{d.Q, d.ldq}, Z{d.Z, d.ldz};
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -170,94 +190,103 @@ __device__ void ht_pair(const HtDesc& d, bool want_qz, int z_init, int* info_b, 
     __syncthreads();
   }
 
-  // ---- stage 2: zero A below the subdiagonal, keep R triangular
+  // ---- stage 2: zero A below the subdiagonal, keep R triangular.  Thread 0
+  // builds step i's rotation pair during step i + 1 (double-buffered in
+  // shared memory), from values it carries or owns: A[i-1, j] (untouched
+  // until step i), A[i, j] (the left rotation of step i + 1 applied to the
+  // pair it carries), R[i-1, i-1] (untouched), R[i-1, i] (the right rotation
+  // of step i + 1 on row i - 1, its own item) and R[i, i] (the 2x2 block of
+  // step i + 1, its own item).  The other threads apply the current pair.
   for (int j = 0; j + 2 < n; ++j) {
-    for (int i = n - 1; i >= j + 2; --i) {
-      // thread 0 builds the rotation pair (one FP64 chain; computing it in
-      // every thread would cost the SM's FP64 pipe NT times as much)
+    double aa = 0.0, bb = 0.0;   // thread 0: the (A[i-1, j], A[i, j]) the current pair was built from
+    if (tid == 0) {
+      const int i = n - 1;
+      aa = A(i - 1, j);
+      bb = A(i, j);
+      ht_build_pair(aa, bb, B(i - 1, i - 1), B(i - 1, i), B(i, i), rotb[0]);
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int i = n - 1; i >= j + 2; --i, buf ^= 1) {
+      const double c1 = rotb[buf][0], s1 = rotb[buf][1], c2 = rotb[buf][2], s2 = rotb[buf][3];
       if (tid == 0) {
-        double c1, s1, c2, s2;
-        ht_rot_second(A(i - 1, j), A(i, j), c1, s1);
+        // the 2x2 blocks on rows and columns (i-1, i): left rotation, then right
+        const double a11 = A(i - 1, i - 1), a12 = A(i - 1, i), a21 = A(i, i - 1), a22 = A(i, i);
+        const double t11 = fma(c1, a11, s1 * a21), t21 = fma(-s1, a11, c1 * a21);
+        const double t12 = fma(c1, a12, s1 * a22), t22 = fma(-s1, a12, c1 * a22);
+        A(i - 1, i - 1) = fma(c2, t11, s2 * t12);
+        A(i - 1, i) = fma(-s2, t11, c2 * t12);
+        A(i, i - 1) = fma(c2, t21, s2 * t22);
+        A(i, i) = fma(-s2, t21, c2 * t22);
+        // R: the left rotation gives (g11, g12; f21, f22), the right one zeroes f21
         const double r11 = B(i - 1, i - 1), r12 = B(i - 1, i), r22 = B(i, i);
-        const double f21 = -s1 * r11, f22 = fma(-s1, r12, c1 * r22);   // R[i, i-1], R[i, i] after the left rotation
-        ht_rot_first(f21, f22, c2, s2);
-        rot[0] = c1;
-        rot[1] = s1;
-        rot[2] = c2;
-        rot[3] = s2;
-        rot[4] = f21;
-        rot[5] = f22;
-      }
-      __syncthreads();
-      const double c1 = rot[0], s1 = rot[1], c2 = rot[2], s2 = rot[3];
-      // work items: [A left: columns j..n-1 except i-1, i] [R left: columns i+1..n-1]
-      // [A right: rows except i-1, i] [R right: rows 0..i-2] [Q: rows] [Z: rows] [2x2 blocks]
-      const int nal = n - j - 2, nrl = n - i - 1, nar = n - 2, nrr = i - 1;
-      const int nq = want_qz ? n : 0;
-      const int total = nal + nrl + nar + nrr + 2 * nq + 1;
-      for (int t = tid; t < total; t += NT) {
-        int u = t;
-        if (u < nal) {
-          const int c = (u < i - 1 - j) ? j + u : u + j + 2;   // skip columns i-1, i
-          const double x = A(i - 1, c), y = A(i, c);
-          A(i - 1, c) = fma(c1, x, s1 * y);
-          A(i, c) = (c == j) ? 0.0 : fma(-s1, x, c1 * y);
-          continue;
+        const double f21 = rotb[buf][4], f22 = rotb[buf][5];
+        const double g11 = c1 * r11, g12 = fma(c1, r12, s1 * r22);
+        const double n11 = fma(c2, g11, s2 * g12);
+        B(i - 1, i - 1) = n11;
+        B(i - 1, i) = fma(-s2, g11, c2 * g12);
+        B(i, i - 1) = 0.0;
+        B(i, i) = fma(-s2, f21, c2 * f22);
+        // the right rotation on R's row i - 2
+        const double x = B(i - 2, i - 1), y = B(i - 2, i);
+        const double m12 = fma(c2, x, s2 * y);
+        B(i - 2, i - 1) = m12;
+        B(i - 2, i) = fma(-s2, x, c2 * y);
+        if (i - 1 >= j + 2) {   // the next step's pair
+          const double na = A(i - 2, j), nb = fma(c1, aa, s1 * bb);
+          ht_build_pair(na, nb, B(i - 2, i - 2), m12, n11, rotb[buf ^ 1]);
+          aa = na;
+          bb = nb;
         }
-        u -= nal;
-        if (u < nrl) {
-          const int c = i + 1 + u;
-          const double x = B(i - 1, c), y = B(i, c);
-          B(i - 1, c) = fma(c1, x, s1 * y);
-          B(i, c) = fma(-s1, x, c1 * y);
-          continue;
-        }
-        u -= nrl;
-        if (u < nar) {
-          const int r = (u < i - 1) ? u : u + 2;   // skip rows i-1, i
-          const double x = A(r, i - 1), y = A(r, i);
-          A(r, i - 1) = fma(c2, x, s2 * y);
-          A(r, i) = fma(-s2, x, c2 * y);
-          continue;
-        }
-        u -= nar;
-        if (u < nrr) {
-          const int r = u;
-          const double x = B(r, i - 1), y = B(r, i);
-          B(r, i - 1) = fma(c2, x, s2 * y);
-          B(r, i) = fma(-s2, x, c2 * y);
-          continue;
-        }
-        u -= nrr;
-        if (u < nq) {
-          const double x = Q(u, i - 1), y = Q(u, i);
-          Q(u, i - 1) = fma(c1, x, s1 * y);
-          Q(u, i) = fma(-s1, x, c1 * y);
-          continue;
-        }
-        u -= nq;
-        if (u < nq) {
+      } else {
+        // work items: [A left: columns j..n-1 except i-1, i] [R left: columns i+1..n-1]
+        // [A right: rows except i-1, i] [R right: rows 0..i-3] [Q: rows] [Z: rows]
+        const int nal = n - j - 2, nrl = n - i - 1, nar = n - 2, nrr = i - 2;
+        const int nq = want_qz ? n : 0;
+        const int total = nal + nrl + nar + nrr + 2 * nq;
+        for (int t = tid - 1; t < total; t += NT - 1) {
+          int u = t;
+          if (u < nal) {
+            const int c = (u < i - 1 - j) ? j + u : u + j + 2;   // skip columns i-1, i
+            const double x = A(i - 1, c), y = A(i, c);
+            A(i - 1, c) = fma(c1, x, s1 * y);
+            A(i, c) = (c == j) ? 0.0 : fma(-s1, x, c1 * y);
+            continue;
+          }
+          u -= nal;
+          if (u < nrl) {
+            const int c = i + 1 + u;
+            const double x = B(i - 1, c), y = B(i, c);
+            B(i - 1, c) = fma(c1, x, s1 * y);
+            B(i, c) = fma(-s1, x, c1 * y);
+            continue;
+          }
+          u -= nrl;
+          if (u < nar) {
+            const int r = (u < i - 1) ? u : u + 2;   // skip rows i-1, i
+            const double x = A(r, i - 1), y = A(r, i);
+            A(r, i - 1) = fma(c2, x, s2 * y);
+            A(r, i) = fma(-s2, x, c2 * y);
+            continue;
+          }
+          u -= nar;
+          if (u < nrr) {
+            const double x = B(u, i - 1), y = B(u, i);
+            B(u, i - 1) = fma(c2, x, s2 * y);
+            B(u, i) = fma(-s2, x, c2 * y);
+            continue;
+          }
+          u -= nrr;
+          if (u < nq) {
+            const double x = Q(u, i - 1), y = Q(u, i);
+            Q(u, i - 1) = fma(c1, x, s1 * y);
+            Q(u, i) = fma(-s1, x, c1 * y);
+            continue;
+          }
+          u -= nq;
           const double x = Z(u, i - 1), y = Z(u, i);
           Z(u, i - 1) = fma(c2, x, s2 * y);
           Z(u, i) = fma(-s2, x, c2 * y);
-          continue;
-        }
-        // the 2x2 blocks on rows and columns (i-1, i): left rotation, then right
-        {
-          double a11 = A(i - 1, i - 1), a12 = A(i - 1, i), a21 = A(i, i - 1), a22 = A(i, i);
-          double t11 = fma(c1, a11, s1 * a21), t21 = fma(-s1, a11, c1 * a21);
-          double t12 = fma(c1, a12, s1 * a22), t22 = fma(-s1, a12, c1 * a22);
-          A(i - 1, i - 1) = fma(c2, t11, s2 * t12);
-          A(i - 1, i) = fma(-s2, t11, c2 * t12);
-          A(i, i - 1) = fma(c2, t21, s2 * t22);
-          A(i, i) = fma(-s2, t21, c2 * t22);
-          // R: the left rotation gives (r11', r12'; f21, f22), the right one zeroes f21
-          const double r11 = B(i - 1, i - 1), r12 = B(i - 1, i), r22 = B(i, i), f21 = rot[4], f22 = rot[5];
-          const double g11 = c1 * r11, g12 = fma(c1, r12, s1 * r22);
-          B(i - 1, i - 1) = fma(c2, g11, s2 * g12);
-          B(i - 1, i) = fma(-s2, g11, c2 * g12);
-          B(i, i - 1) = 0.0;
-          B(i, i) = fma(-s2, f21, c2 * f22);
         }
       }
       __syncthreads();
@@ -270,10 +299,10 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_ht(const HtDesc* __restrict__ descs, int nb, int want_qz, int z_init,
                                            int* __restrict__ info) {
   __shared__ double red[NT / 32];
-  __shared__ double rot[6];
+  __shared__ double rotb[2][8];
   for (int b = blockIdx.x; b < nb; b += gridDim.x) {
     const HtDesc d = descs[b];
-    ht_pair<NT>(d, want_qz != 0 && d.Q != nullptr, z_init, info + b, red, rot);
+    ht_pair<NT>(d, want_qz != 0 && d.Q != nullptr, z_init, info + b, red, rotb);
     __syncthreads();
   }
 }
