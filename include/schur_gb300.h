@@ -29,7 +29,9 @@
  *  - Scratch: if opts->workspace is non-NULL and opts->workspace_bytes is at
  *    least the size reported by the matching *_workspace_size call, the
  *    library allocates no device memory; otherwise it allocates (and frees)
- *    its own scratch inside the call.
+ *    its own scratch inside the call.  A caller workspace must be 256-byte
+ *    aligned (cudaMalloc's alignment); a smaller or misaligned one returns
+ *    SCHUR_ERR_WORKSPACE before any device work.
  *  - Return codes: SCHUR_OK (0) on success; a negative value -(i) when
  *    argument i (1-based) is invalid; SCHUR_ERR_* below for other errors;
  *    a positive value k > 0 when the iteration limit was reached: rows

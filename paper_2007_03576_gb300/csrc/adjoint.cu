@@ -462,13 +462,12 @@ int run_backward(const std::vector<AdjMatrix>& ms, const schur_opts* opts) {
   char* mem = nullptr;
   bool own = false;
   int rc = SCHUR_OK;
+  if (o.workspace && schur::workspace_unusable(o, need)) return SCHUR_ERR_WORKSPACE;
   try {
     schur::init_kernel_attributes();
     adj_raise_limit();
-    if (o.workspace && o.workspace_bytes >= need) {
+    if (o.workspace) {
       mem = (char*)o.workspace;
-    } else if (o.workspace) {
-      return SCHUR_ERR_WORKSPACE;
     } else {
       if (cudaMalloc((void**)&mem, need) != cudaSuccess) {
         cudaGetLastError();
@@ -634,7 +633,7 @@ int run_backward_blocked(const AdjMatrix& m, const schur_opts* opts) {
   char* mem = nullptr;
   bool own = false;
   if (o.workspace) {
-    if (o.workspace_bytes < L.total) return SCHUR_ERR_WORKSPACE;
+    if (schur::workspace_unusable(o, L.total)) return SCHUR_ERR_WORKSPACE;
     mem = (char*)o.workspace;
   } else {
     if (cudaMalloc((void**)&mem, L.total) != cudaSuccess) {

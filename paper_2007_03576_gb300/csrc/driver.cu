@@ -458,11 +458,11 @@ void Solver::drain_z() {
 }
 
 int Solver::setup(int n) {
-  init_kernel_attributes();
   size_t need = workspace_bytes(n, opts);
+  if (opts.workspace != nullptr && workspace_unusable(opts, need)) return SCHUR_ERR_WORKSPACE;
+  init_kernel_attributes();
   char* base = nullptr;
   if (opts.workspace != nullptr) {
-    if (opts.workspace_bytes < need) return SCHUR_ERR_WORKSPACE;
     base = (char*)opts.workspace;
   } else {
     if (cudaMalloc((void**)&owned, need) != cudaSuccess) {

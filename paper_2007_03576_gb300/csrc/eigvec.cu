@@ -402,7 +402,7 @@ extern "C" int schur_eigenvectors(int n, const double* S, int lds, const double*
   char* mem = nullptr;
   bool own = false;
   if (o.workspace) {
-    if (o.workspace_bytes < need) return SCHUR_ERR_WORKSPACE;
+    if (schur::workspace_unusable(o, need)) return SCHUR_ERR_WORKSPACE;
     mem = (char*)o.workspace;
   } else {
     if (cudaMalloc((void**)&mem, need) != cudaSuccess) {

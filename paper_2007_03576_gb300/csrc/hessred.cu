@@ -296,7 +296,7 @@ extern "C" int schur_hessenberg_reduce(int n, double* A, int lda, double* Q, int
   char* mem = nullptr;
   bool own = false;
   if (o.workspace) {
-    if (o.workspace_bytes < need) return SCHUR_ERR_WORKSPACE;
+    if (schur::workspace_unusable(o, need)) return SCHUR_ERR_WORKSPACE;
     mem = (char*)o.workspace;
   } else {
     if (cudaMalloc((void**)&mem, need) != cudaSuccess) {

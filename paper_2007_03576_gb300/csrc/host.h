@@ -168,6 +168,12 @@ int num_sms();                   // SMs of the current device
 void read_opts(const schur_opts* in, schur_opts* out);
 void default_ns_nw(int m, int* ns, int* nw);
 size_t workspace_bytes(int n, const schur_opts& o);
+// A caller workspace (o.workspace non-NULL) that cannot hold `need` bytes or
+// is not 256-byte aligned (buffers are laid out at 256-byte offsets from it,
+// so a misaligned base would misalign every FP64 access).
+inline bool workspace_unusable(const schur_opts& o, size_t need) {
+  return o.workspace_bytes < need || ((size_t)o.workspace & 255) != 0;
+}
 const char* status_string(int code);
 
 // Right eigenvectors of a standardised quasi-triangular S, the work of

@@ -323,7 +323,7 @@ int run_ht(const std::vector<HtPair>& ps, int* info_out, const schur_opts* opts)
   char* mem = nullptr;
   bool own = false;
   if (o.workspace) {
-    if (o.workspace_bytes < need) return SCHUR_ERR_WORKSPACE;
+    if (schur::workspace_unusable(o, need)) return SCHUR_ERR_WORKSPACE;
     mem = (char*)o.workspace;
   } else {
     if (cudaMalloc((void**)&mem, need) != cudaSuccess) {

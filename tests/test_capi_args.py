@@ -270,3 +270,31 @@ def test_short_opts_struct_keeps_defaults_beyond_its_size():
     assert lib.schur_hessenberg(N, DEV, N, None, N, DEV, DEV, ob) == -4
     assert lib.schur_qz(N, DEV, N, DEV, N, None, N, None, N, DEV, DEV, DEV, ob) == -6
     assert lib.schur_ht_reduce(N, DEV, N, DEV, N, None, N, None, N, ob) == -6
+
+
+def test_misaligned_or_small_workspace_is_refused():
+    """A caller workspace must be 256-byte aligned: a misaligned one (large
+    enough) and an aligned one that is too small both return
+    SCHUR_ERR_WORKSPACE before any device work, in every entry point that
+    takes scratch from opts."""
+    lib = _lib.load()
+    calls = {
+        "schur_eigenvectors": lambda ob: lib.schur_eigenvectors(N, DEV, N, DEV, N, DEV, DEV, DEV, N, ob),
+        "schur_hessenberg_reduce": lambda ob: lib.schur_hessenberg_reduce(N, DEV, N, DEV, N, ob),
+        "schur_ht_reduce": lambda ob: lib.schur_ht_reduce(N, DEV, N, DEV, N, DEV, N, DEV, N, ob),
+        "schur_qz": lambda ob: lib.schur_qz(N, DEV, N, DEV, N, DEV, N, DEV, N, DEV, DEV, DEV, ob),
+        "schur_factor_backward": lambda ob: lib.schur_factor_backward(N, DEV, N, DEV, N, DEV, N, DEV, N, DEV, N,
+                                                                      ob),
+        "schur_eig_backward (per-warp path)": lambda ob: lib.schur_eig_backward(N, DEV, N, DEV, N, DEV, DEV, DEV,
+                                                                               DEV, DEV, N, ob),
+        "schur_eig_backward (blocked path)": lambda ob: lib.schur_eig_backward(2000, DEV, 2000, DEV, 2000, DEV,
+                                                                              DEV, DEV, DEV, DEV, 2000, ob),
+    }
+    for name, call in calls.items():
+        o = _lib.make_opts(0)
+        o.workspace = 4096 + 8
+        o.workspace_bytes = 1 << 40
+        assert call(ctypes.byref(o)) == _lib.SCHUR_ERR_WORKSPACE, name
+        o.workspace = 4096
+        o.workspace_bytes = 8
+        assert call(ctypes.byref(o)) == _lib.SCHUR_ERR_WORKSPACE, name
