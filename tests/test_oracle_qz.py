@@ -165,3 +165,60 @@ def test_standardize_pair_block(seed):
         assert S[1, 0] == 0.0 and T[1, 0] == 0.0
         perm, dist = metrics.match_eigenvalues(ref, np.array([S[0, 0] / T[0, 0], S[1, 1] / T[1, 1]]))
         assert np.max(dist) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_ht_subdiag_negligible_boundaries():
+    """The QZ deflation test on H: an entry just at u (|h_{k-1,k-1}| +
+    |h_kk|) is negligible, one ulp-scale step above it is not; the sum uses
+    both diagonal entries (swapping one for its neighbour moves the
+    boundary); with zero diagonal entries the smlnum floor decides."""
+    from oracle.qr import U, smlnum
+
+    n = 6
+    H = np.triu(np.ones((n, n)), -1)
+    H[2, 2], H[3, 3] = 3.0, 5.0
+    thr = U * (3.0 + 5.0)
+    H[3, 2] = thr
+    assert qz.ht_subdiag_negligible(H, 3, n)
+    H[3, 2] = thr * (1.0 + 4 * U)
+    assert not qz.ht_subdiag_negligible(H, 3, n)
+    H[3, 2] = U * (3.0 + 1.0) * 1.5        # above u (|h22| + |h23|) but below the true threshold
+    assert qz.ht_subdiag_negligible(H, 3, n)
+    H[2, 2] = H[3, 3] = 0.0
+    H[3, 2] = smlnum(n)
+    assert qz.ht_subdiag_negligible(H, 3, n)
+    H[3, 2] = 2.0 * smlnum(n)
+    assert not qz.ht_subdiag_negligible(H, 3, n)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_trailing_shift_pair_against_dense_m(seed):
+    """(ssum, sprod) = trace and determinant of the trailing 2x2 of
+    M = H T^-1 formed with the dense inverse of the whole T (the routine uses
+    only a 3x3 window of T); T = I reduces it to H's trailing 2x2."""
+    rng = np.random.default_rng(70 + seed)
+    n = 9
+    H = np.triu(rng.standard_normal((n, n)), -1)
+    T = np.triu(rng.standard_normal((n, n))) + 3.0 * np.eye(n)
+    for lo, hi in [(0, n - 1), (2, 6), (4, 6)]:
+        M = H @ np.linalg.inv(T)
+        m = M[hi - 1:hi + 1, hi - 1:hi + 1]
+        ssum, sprod = qz.trailing_shift_pair(H, T, lo, hi)
+        assert abs(ssum - np.trace(m)) <= 1e-12 * np.abs(m).sum()
+        assert abs(sprod - np.linalg.det(m)) <= 1e-12 * np.abs(m).sum() ** 2
+    ssum, sprod = qz.trailing_shift_pair(H, np.eye(n), 0, n - 1)
+    h = H[n - 2:, n - 2:]
+    assert abs(ssum - np.trace(h)) <= 1e-14 * np.abs(h).sum()
+    assert abs(sprod - np.linalg.det(h)) <= 1e-13 * np.abs(h).sum() ** 2
+
+
+def test_exceptional_shift_pair_with_identity_t_is_the_qr_one():
+    """T = I: the generalized exceptional pair equals the standard QR
+    iteration's (EISPACK's constants, pinned with the n-cycle matrix)."""
+    rng = np.random.default_rng(80)
+    n = 8
+    H = np.triu(rng.standard_normal((n, n)), -1)
+    for lo, hi in [(0, n - 1), (3, 6), (5, 6)]:
+        got = qz.exceptional_shift_pair(H, np.eye(n), lo, hi)
+        want = qr.exceptional_pairs(H, lo, hi, 1)[0]
+        assert np.allclose(got, want, rtol=1e-15, atol=0.0)
