@@ -672,3 +672,27 @@ def test_recompute_shifts_run_is_a_valid_schur_form():
     assert info == 0 and st.sweeps - st.sweeps // 6 <= st.recomputed <= st.sweeps
     _check_schur(H, S, Z)
     _eig_close(wr + 1j * wi, scipy.linalg.eigvals(H), 1e-9 * np.linalg.norm(H))
+
+
+def test_accuracy_metrics_closed_forms():
+    """Sec. 5.4's metrics on cases with a known value: R_A of a
+    factorisation off by one entry, R_orth of a scaled identity, E_lambda
+    of eigenvalues moved by a known relative amount."""
+    from oracle import metrics
+    from oracle.qr import U
+
+    rng = np.random.default_rng(91)
+    n = 7
+    A = rng.standard_normal((n, n))
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    X = Q.T @ A @ Q
+    E = np.zeros((n, n))
+    E[2, 5] = 3e-10                      # far above the rounding of Q X Q^T (a few u ||A||)
+    want = 3e-10 / (U * np.linalg.norm(A))  # ||Q E Q^T||_F = ||E||_F
+    assert abs(metrics.r_a(A, X + E, Q) - want) <= 1e-3 * want
+    eps = 1e-12
+    want = np.sqrt(n) * ((1 + eps) ** 2 - 1) / (U * np.sqrt(n))
+    assert abs(metrics.r_orth((1 + eps) * np.eye(n)) - want) <= 1e-3 * want
+    exact = np.array([1.0, -2.0, 3.0 + 4.0j])
+    comp = exact * (1 + np.array([2.0, 5.0, 7.0]) * U)
+    assert np.allclose(metrics.e_lambda(comp, exact), [2.0, 5.0, 7.0], rtol=1e-6)
