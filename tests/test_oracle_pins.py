@@ -693,6 +693,6 @@ def test_accuracy_metrics_closed_forms():
     eps = 1e-12
     want = np.sqrt(n) * ((1 + eps) ** 2 - 1) / (U * np.sqrt(n))
     assert abs(metrics.r_orth((1 + eps) * np.eye(n)) - want) <= 1e-3 * want
-    exact = np.array([1.0, -2.0, 3.0 + 4.0j])
-    comp = exact * (1 + np.array([2.0, 5.0, 7.0]) * U)
+    exact = np.array([1.0, -2.0, 4.0j])
+    comp = exact * (1 + np.array([2.0, 5.0, 7.0]) * U)   # exact in binary64: 2, 5, 7 ulps of 1, 2, 4
     assert np.allclose(metrics.e_lambda(comp, exact), [2.0, 5.0, 7.0], rtol=1e-6)
